@@ -1,0 +1,415 @@
+"""Benchmark of the fused D2Q9 relative-velocity step on GB300.
+
+Headline workload: D2Q9 FP32, 4096 x 4096 periodic, Taylor-Green vortex u0 = 0.04,
+rho0 = 1, s = (0,0,0,1.4,1.8,1.8,1.2,1.2,1.4) (s_nu = 1.8), prescribed relative velocity
+u~(x,t) = 0.03 (cos 2 pi y/L, sin 2 pi x/L) cos(2 pi t / 1000). One bench step is one
+time step (pull transport + relaxation in the moving frame), one kernel launch. The
+1.2 GB state is larger than L2, so no flush is needed between steps.
+
+``python bench.py [--gpus N] [--steps K] [--warmup W]`` prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (same metric).
+With N > 1 (torchrun) every rank advances its own replica of the lattice (weak scaling;
+the step has no exchange across replicas).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and fraction of HBM roofline, relative-velocity step vs plain MRT"
+L = 4096
+S_RATES = [0, 0, 0, 1.4, 1.8, 1.8, 1.2, 1.2, 1.4]
+UT_AMP, UT_PERIOD = 0.03, 1000.0
+BYTES_PER_NODE = {"fp32": 72, "fp16": 36, "bf16": 36}
+WORKLOAD = ("D2Q9 relative-velocity step, FP32, 4096x4096 periodic, Taylor-Green u0=0.04, "
+            "s_nu=1.8, prescribed u~ = 0.03 (cos 2pi y/L, sin 2pi x/L) cos(2pi t/1000)")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "d2q9_step_tg4096_traffic.txt")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1312_3297_gb300", "csrc", f)
+                  for f in ("d2q9.cuh", "d2q9_kernels.cu")]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """Per-launch DRAM bytes of the step kernel from the committed ncu summary, if the
+    kernel sources are unchanged since it was taken; else None."""
+    try:
+        kv = {}
+        with open(TRAFFIC_FILE) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("kernel_sources_sha256_16") != kernel_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the GPU is busy."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="lbmrv_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 5.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
+
+    def mark(self) -> int:
+        try:
+            with open(self.path) as fh:
+                return sum(1 for _ in fh)
+        except OSError:
+            return 0
+
+    def stop(self):
+        if self.proc is not None:
+            time.sleep(0.06)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, first_line: int, last_line: int):
+        rows = []
+        try:
+            with open(self.path) as fh:
+                lines = fh.read().splitlines()
+        except OSError:
+            lines = []
+        sel = lines[first_line:last_line + 1] or lines[-3:]
+        for ln in sel:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ distributed
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ GPU arm
+def time_steps(sim, steps: int, torch):
+    """Device time (ms) of `steps` fused steps on the handle's stream, CUDA events."""
+    st = sim.stream
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    sim.step(steps)
+    b.record(st)
+    b.synchronize()
+    return a.elapsed_time(b)
+
+
+def make_sim(torch, D2Q9, inp, storage, mode, size, fields):
+    sim = D2Q9(size, size, S_RATES, mode=mode, storage=storage)
+    if mode == "prescribed":
+        sim.set_utilde(None, UT_AMP, UT_PERIOD)
+    rho, ux, uy = (torch.as_tensor(fields[k], dtype=torch.float32) for k in ("rho", "ux", "uy"))
+    sim.init_equilibrium(rho, ux, uy)
+    return sim
+
+
+def side_measure(torch, D2Q9, inp, storage, mode, size, fields, steps, peak):
+    sim = make_sim(torch, D2Q9, inp, storage, mode, size, fields)
+    sim.step(3)
+    ms = time_steps(sim, steps, torch)
+    sim.close()
+    n = size * size
+    per = ms / steps
+    gbs = BYTES_PER_NODE[storage] * n / (per * 1e-3) / 1e9
+    return {"mlups": round(n / (per * 1e-3) / 1e6, 1), "ms_per_step": round(per, 5),
+            "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import lbm_inputs as inp
+    from paper_1312_3297_gb300 import D2Q9, binding
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    binding.load()
+    peak, peak_kind = measured_peaks()
+    n = L * L
+    fields = inp.taylor_green(L, L, u0=0.04)
+    sim = make_sim(torch, D2Q9, inp, "fp32", "prescribed", L, fields)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        first = clocks.mark()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ms = time_steps(sim, args.steps, torch)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    wall_ms = (time.perf_counter() - t_wall) * 1e3
+    if clocks:
+        last = clocks.mark()
+        clocks.stop()
+        clock_info = clocks.summary(first, last)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    finite = sim.conserved(allow_nonfinite=True)
+    sim.close()
+    per_step_ms = ms / args.steps
+    mlups = world * n * args.steps / (ms * 1e-3) / 1e6
+    achieved = BYTES_PER_NODE["fp32"] * n / (per_step_ms * 1e-3) / 1e9
+    out = None
+    if rank == 0:
+        extras = {}
+        if not args.no_extras and world == 1:
+            k = max(50, min(args.steps, 300))
+            extras["plain_mrt_u0"] = side_measure(torch, D2Q9, inp, "fp32", "zero", L, fields,
+                                                  k, peak)
+            extras["relative_u_fluid"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", L,
+                                                      fields, k, peak)
+            extras["relative_u_prescribed"] = {
+                "mlups": round(n / (per_step_ms * 1e-3) / 1e6, 1),
+                "ms_per_step": round(per_step_ms, 5), "gbs": round(achieved, 1),
+                "frac": round(achieved / peak, 4)}
+            big = inp.perturbed_uniform(8192, 8192, seed=0)
+            for st in ("fp16", "bf16"):
+                extras[f"precision_{st}_8192"] = side_measure(torch, D2Q9, inp, st, "fluid",
+                                                              8192, big, k, peak)
+            extras["fp32_fluid_8192"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", 8192,
+                                                     big, k, peak)
+            del big
+        e2e = e2e_measure(torch, D2Q9, inp, fields, args.steps) if not args.no_e2e else None
+        cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
+        out = {
+            "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "nodes": n, "bytes_per_node_step": 72,
+                       "l2": "state 1.2 GB > 129 MB L2; no flush needed",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": recorded_traffic(), "peak_kind": peak_kind,
+                         "kernel": "k_step_vec<float,4,analytic>"},
+            "clocks": clock_info,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "cpu_baseline": cpu,
+            "modes": extras,
+            "wall_ms_timed_region": round(wall_ms, 2),
+            "nonfinite_nodes": finite[3],
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+def e2e_measure(torch, D2Q9, inp, fields, steps):
+    """Through the public API with host buffers: pinned host fields -> device,
+    equilibrium, `steps` steps, moments back to pinned host memory."""
+    n = L * L
+    rho_h = torch.as_tensor(fields["rho"], dtype=torch.float32).reshape(-1).pin_memory()
+    u_h = torch.stack([torch.as_tensor(fields["ux"], dtype=torch.float32),
+                       torch.as_tensor(fields["uy"], dtype=torch.float32)]).reshape(2, -1)
+    u_h = u_h.pin_memory()
+    rho_o = torch.empty((L, L), dtype=torch.float32, pin_memory=True)
+    u_o = torch.empty((2, L, L), dtype=torch.float32, pin_memory=True)
+    sim = D2Q9(L, L, S_RATES, mode="prescribed", storage="fp32")
+    sim.set_utilde(None, UT_AMP, UT_PERIOD)
+    sim.init_equilibrium_host(rho_h, u_h)
+    sim.step(3)
+    sim.moments_host(rho_o, u_o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.init_equilibrium_host(rho_h, u_h)
+    sim.step(steps)
+    sim.moments_host(rho_o, u_o)  # synchronous
+    dt = time.perf_counter() - t0
+    sim.close()
+    return {"value": round(n * steps / dt / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": round(12 * n / steps, 1),
+            "d2h_bytes_per_step": round(12 * n / steps, 1),
+            "unit_of_work": f"one {steps}-step run from host rho,u to host rho,u"}
+
+
+# ------------------------------------------------------------------ CPU oracle
+class OracleBand:
+    """The FP64 definition oracle (per-node M(u~) and LU solve) advancing a 4096-wide
+    periodic band of `rows` rows of the Taylor-Green workload (prescribed u~ evaluated
+    at the band's global coordinates), with `threads` OpenMP threads."""
+
+    def __init__(self, rows: int, threads: int):
+        import numpy as np
+
+        import oracle
+
+        self.oracle, self.np = oracle, np
+        self.rows, self.threads, self.t = rows, threads, 1
+        x = np.arange(L, dtype=np.float64)[None, :]
+        y = np.arange(rows, dtype=np.float64)[:, None]
+        k = 2 * np.pi / L
+        ux = -0.04 * np.cos(k * x) * np.sin(k * y)
+        uy = 0.04 * np.sin(k * x) * np.cos(k * y)
+        rho = 1.0 + 3.0 * (-0.04 ** 2 / 4.0 * (np.cos(2 * k * x) + np.cos(2 * k * y)))
+        self.f = oracle.init_equilibrium(rho, ux, uy, 1.0)
+        self.work = np.empty_like(self.f)
+        self.ut0 = np.stack([np.cos(k * y) * np.ones((1, L)), np.sin(k * x) * np.ones((rows, 1))])
+        self.s = np.array(S_RATES, float)
+
+    def step(self) -> float:
+        t0 = time.perf_counter()
+        self.oracle.run_inplace(self.f, self.work, 1.0, self.s, self.oracle.MODE_PRESCRIBED, 1,
+                                t0=self.t, method=self.oracle.METHOD_DEFINITION, ut0=self.ut0,
+                                amp=UT_AMP, period=UT_PERIOD, nthreads=self.threads)
+        self.t += 1
+        return time.perf_counter() - t0
+
+
+def _oracle_threads():
+    import oracle
+
+    oracle.build()
+    return (os.cpu_count() or 1) if oracle.openmp_enabled() else 1
+
+
+def _calibrated_rows(threads: int, seconds_per_step: float) -> int:
+    probe = OracleBand(16, threads)
+    probe.step()
+    rate = 16 * L / probe.step()  # nodes per second
+    return int(max(1, min(L, seconds_per_step * rate / L)))
+
+
+def cpu_baseline_measure(target_s: float = 15.0):
+    threads = _oracle_threads()
+    rows = _calibrated_rows(threads, target_s)
+    band = OracleBand(rows, threads)
+    dt = band.step()
+    return {"value": round(rows * L / dt / 1e6, 3), "unit": "MLUPS", "cores": threads,
+            "kind": "oracle",
+            "sample": (f"one time step of a {L}x{rows} periodic band of the 4096^2 "
+                       f"Taylor-Green workload, FP64 definition oracle (per-node M(u~) "
+                       f"and LU solve), {dt:.1f} s")}
+
+
+def reference_arm(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    threads = _oracle_threads()
+    rows = _calibrated_rows(threads, 120.0 / (args.steps + args.warmup))
+    band = OracleBand(rows, threads)
+    for _ in range(args.warmup):
+        band.step()
+    total = sum(band.step() for _ in range(args.steps))
+    per = total / args.steps
+    value = rows * L / per / 1e6
+    sample = (f"each step: one time step of a {L}x{rows} periodic band of the 4096^2 "
+              f"Taylor-Green workload, FP64 definition oracle")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "MLUPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(per * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample_rows": rows},
+        "cpu_baseline": {"value": round(value, 4), "unit": "MLUPS", "cores": threads,
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

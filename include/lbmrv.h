@@ -1,0 +1,186 @@
+/*
+ * lbmrv — lattice Boltzmann schemes with relative velocities on one GB300 (sm_103a).
+ *
+ * C ABI of the library. The method is that of F. Dubois, T. Fevrier and B. Graille,
+ * "Lattice Boltzmann schemes with relative velocities" (arXiv:1312.3297):
+ *   - Section 1.1: a time step is a local relaxation in moment space followed by the
+ *     exact transport f_j(x, t+dt) = f*_j(x - v_j dt, t) (relation (transport));
+ *   - Section 1.2: the moments are taken in a frame moving at a relative velocity u~,
+ *     m(u~) = M(u~) f with M(u~)_kj = P_k(v_j - u~) (relations (MatMu), (ftomu)),
+ *     relaxed diagonally towards m_eq(u~) = M(u~) f_eq (relation (relaxationu)),
+ *     and mapped back f* = M(u~)^{-1} m*;
+ *   - Section 1.3: for D2Q9 with the orthogonal moments of relation (mom),
+ *     M(u~) = T(u~) M(0) with the lower block-triangular shifting matrix T(u~)
+ *     (relation (matTu), Appendix A) and T(u~)^{-1} = T(-u~) (morphism proposition).
+ * u~ = 0 is d'Humieres' MRT scheme; u~ = q/rho is the cascaded-like choice; u~ may also
+ * be a prescribed field u~(x, t).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: LBMRV_OK (0) or a negative LBMRV_E_* status. Nothing is thrown
+ *     across the ABI. lbmrv_last_error() gives a one-line message for the last failure.
+ *   - Pointers named *_dev are device pointers (CUDA global memory of the handle's
+ *     device); pointers named *_host are host pointers. Caller-owned buffers are never
+ *     freed or retained by the library beyond the call, except the buffers passed to
+ *     lbmrv_create and lbmrv_set_utilde, which must outlive the handle (or the next
+ *     lbmrv_set_utilde call).
+ *   - Work is enqueued on the handle's CUDA stream and returns without synchronising,
+ *     except the calls documented as synchronous (they return host values).
+ *   - Lattice layout: periodic D2Q9, dims = {nx, ny, 1}, lattice units dx = 1 (so
+ *     dt = 1/lambda, relation (lambda)). Node (x, y) has index i = y*nx + x.
+ *     Population state: structure of arrays, 9 planes of nx*ny elements, plane j holds
+ *     velocity j in the order (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
+ *     (times lambda) of Section 1.3. Element i of plane j is at offset j*nx*ny + i.
+ *   - Stored value: g_j = f_j - w_j * rho_ref with w = (4/9, 1/9 x4, 1/36 x4), in the
+ *     storage type of the handle (FP32, FP16 or BF16, round-to-nearest-even). With
+ *     rho_ref = 0 the store holds f itself. All arithmetic is FP32.
+ *   - The state kept by the handle after k steps is the POST-relaxation state
+ *     S_k = C_k(f(k)) at time k: one lbmrv_step pulls the neighbours' S_{k-1}
+ *     (transport) and relaxes at time k. Moments (rho, q) of S_k equal those of f(k),
+ *     since relaxation conserves them.
+ */
+#ifndef LBMRV_H
+#define LBMRV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBMRV_VERSION 1
+
+#if defined(__GNUC__)
+#define LBMRV_API __attribute__((visibility("default")))
+#else
+#define LBMRV_API
+#endif
+
+/* Status codes. */
+#define LBMRV_OK 0
+#define LBMRV_E_INVAL (-1)       /* an argument is out of range or inconsistent */
+#define LBMRV_E_CUDA (-2)        /* a CUDA runtime call or kernel launch failed */
+#define LBMRV_E_NOMEM (-3)       /* device allocation failed, or a workspace is too small */
+#define LBMRV_E_NONFINITE (-4)   /* a NaN or infinity was found in the state */
+#define LBMRV_E_TIMEOUT (-5)     /* reserved: no entry point waits on the device */
+#define LBMRV_E_UNSUPPORTED (-6) /* valid request that this build does not implement */
+
+/* Lattices. */
+#define LBMRV_D2Q9 0
+#define LBMRV_D3Q19 1 /* not built: lbmrv_create returns LBMRV_E_UNSUPPORTED */
+
+/* Choice of the relative velocity u~ (Section 1.2, Introduction). */
+#define LBMRV_UT_ZERO 0       /* u~ = 0: d'Humieres MRT */
+#define LBMRV_UT_FLUID 1      /* u~ = q/rho of the node being relaxed */
+#define LBMRV_UT_PRESCRIBED 2 /* u~(x, t) = A u~0(x) cos(2 pi t / P), see lbmrv_set_utilde */
+
+/* Population storage types. */
+#define LBMRV_FP32 0
+#define LBMRV_FP16 1
+#define LBMRV_BF16 2
+
+typedef struct lbmrv_s* lbmrv_t;
+
+/* Library version (LBMRV_VERSION). */
+LBMRV_API int lbmrv_version(void);
+
+/* Bytes of one population state (9 * nx * ny * element size) for the given lattice,
+ * dims and storage; -1 on invalid arguments. */
+LBMRV_API int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int storage);
+
+/* Create a simulation handle on the current CUDA device.
+ *   lattice  LBMRV_D2Q9.
+ *   dims     {nx, ny, 1}, nx, ny >= 1, nx*ny < 2^31.
+ *   lambda   velocity scale lambda > 0 (relation (lambda)).
+ *   s        9 relaxation rates in the moment order of relation (mom): rho, q_x, q_y,
+ *            e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps. s[0..2] must be 0 (conserved
+ *            moments, Section 1.1); the others are finite.
+ *   umode    LBMRV_UT_* (prescribed mode: see lbmrv_set_utilde; default A = 0).
+ *   storage  LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16.
+ *   rho_ref  reference density of the stored deviation g = f - w rho_ref (0 stores f).
+ *   stream   cudaStream_t to enqueue on (NULL: the legacy default stream).
+ *   f_a_dev, f_b_dev
+ *            two device buffers of lbmrv_state_bytes() each, 16-byte aligned, owned by
+ *            the caller and used as the A-B pair of the pull step; or both NULL, and
+ *            the library allocates (and later frees) them.
+ * The handle also allocates a small reduction buffer (under 64 KB).
+ * Errors: LBMRV_E_INVAL, LBMRV_E_UNSUPPORTED, LBMRV_E_NOMEM, LBMRV_E_CUDA; *out is NULL. */
+LBMRV_API int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda,
+                 const double* s, int umode, int storage, double rho_ref, void* stream,
+                 void* f_a_dev, void* f_b_dev);
+
+/* Release the handle and whatever it allocated. Synchronises its stream. NULL is a no-op. */
+LBMRV_API int lbmrv_destroy(lbmrv_t h);
+
+/* Message of the last failure on h, or of the last failed lbmrv_create on this thread
+ * when h is NULL. Valid until the next call on h. */
+LBMRV_API const char* lbmrv_last_error(lbmrv_t h);
+
+/* Change the stream later work is enqueued on. */
+LBMRV_API int lbmrv_set_stream(lbmrv_t h, void* stream);
+
+/* Kernel variant of the fused step: 0 chooses automatically (the widest aligned pack
+ * that divides nx), 1 forces one node per thread (any lattice), 2/4/8 force that many
+ * consecutive nodes per thread with vector loads (must divide nx; at most 4 for FP32,
+ * 8 for FP16/BF16; the state buffers must be aligned to the pack). All variants compute
+ * the same values; this exists for testing and tuning. */
+LBMRV_API int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread);
+
+/* Prescribed relative velocity u~(x, t) = amplitude * u~0(x) * cos(2 pi t / period),
+ * evaluated at the time index t of each relaxation; period <= 0 means no time factor.
+ *   ut0_dev  device FP32 [2][nx*ny] (x-component plane then y-component plane), kept
+ *            by reference; or NULL for the analytic field u~0 = (cos 2pi y/ny, sin 2pi x/nx).
+ * Only used with LBMRV_UT_PRESCRIBED. */
+LBMRV_API int lbmrv_set_utilde(lbmrv_t h, const float* ut0_dev, double amplitude, double period);
+
+/* Set the state to the equilibrium f_eq(rho, u) at every node and the time to 0:
+ * f_eq,j = w_j rho (1 + 3 v_j.u/l^2 + 9/2 (v_j.u)^2/l^4 - 3/2 |u|^2/l^2), the
+ * second-order polynomial equilibrium (the paper allows any equilibrium independent
+ * of u~, Section 1.2). f_eq is a fixed point of the relaxation for every u~, so it is
+ * also the post-relaxation state at time 0.
+ *   rho_dev  device FP32 [nx*ny], or NULL for rho = 1 everywhere.
+ *   u_dev    device FP32 [2][nx*ny] (u_x plane then u_y plane), physical units. */
+LBMRV_API int lbmrv_init_equilibrium(lbmrv_t h, const float* rho_dev, const float* u_dev);
+
+/* Same from host buffers: copies them into the non-current state buffer on the
+ * handle's stream (no allocation), then builds the equilibrium. Pinned host memory is
+ * faster; the call returns once the copies are enqueued and the host buffers may be
+ * reused only after the stream has synchronised. */
+LBMRV_API int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u_host);
+
+/* Advance n >= 0 time steps. Each step is one fused kernel: pull transport of the
+ * previous post-relaxation state (relation (transport)), then the relaxation in the
+ * frame moving at u~ (relation (relaxationu)) done as
+ *   m0 = M(0) f, d = m0 - m_eq(0), f* = f - M(0)^{-1} T(-u~) S T(u~) d
+ * with T from Appendix A. Step k relaxes at time index t = k. */
+LBMRV_API int lbmrv_step(lbmrv_t h, int64_t n);
+
+/* Density and velocity u = q/rho (relation (rhoq)) of the current state.
+ *   rho_dev  device FP32 [nx*ny] or NULL;  u_dev  device FP32 [2][nx*ny] or NULL. */
+LBMRV_API int lbmrv_moments(lbmrv_t h, float* rho_dev, float* u_dev);
+
+/* Same into host buffers; synchronous. Uses the non-current state buffer as staging. */
+LBMRV_API int lbmrv_moments_host(lbmrv_t h, float* rho_host, float* u_host);
+
+/* Global sums of the current state, accumulated in FP64: out_host[0] = sum rho,
+ * out_host[1..2] = sum q (physical units), out_host[3] = number of nodes holding a
+ * non-finite value. Synchronous. Returns LBMRV_E_NONFINITE (after filling out_host)
+ * when out_host[3] > 0. */
+LBMRV_API int lbmrv_conserved(lbmrv_t h, double out_host[4]);
+
+/* Copy the current stored state (layout above) to / from a device buffer of
+ * lbmrv_state_bytes(). set_state also sets the time index to t. */
+LBMRV_API int lbmrv_get_state(lbmrv_t h, void* dst_dev);
+LBMRV_API int lbmrv_set_state(lbmrv_t h, const void* src_dev, int64_t t);
+
+/* Device pointer of the current state buffer (no copy; valid until the next step). */
+LBMRV_API int lbmrv_state_ptr(lbmrv_t h, void** ptr_out);
+
+/* Time index of the current state (number of steps since the last init/set_state). */
+LBMRV_API int64_t lbmrv_time(lbmrv_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMRV_H */

@@ -223,6 +223,20 @@ def run(f, lam: float, s, mode: int, steps: int, t0: int = 0,
     return f
 
 
+def run_inplace(f: np.ndarray, work: np.ndarray, lam: float, s, mode: int, steps: int,
+                t0: int = 0, method: int = METHOD_DEFINITION, ut0=None, amp: float = 0.0,
+                period: float = 0.0, nthreads: int = 1) -> None:
+    """Same as ``run`` but advances ``f`` in place using the caller's ``work`` buffer."""
+    s = _f64(s)
+    ut0 = None if ut0 is None else _f64(ut0)
+    _, ny, nx = f.shape
+    assert work.shape == f.shape
+    rc = lib().orc_run(method, nx, ny, lam, _ptr(s), mode, _optr(ut0), amp, period, t0,
+                       steps, _ptr(f), _ptr(work), nthreads)
+    if rc != 0:
+        raise FloatingPointError("singular shifted moment matrix")
+
+
 def moments(f, lam: float):
     f = _f64(f)
     _, ny, nx = f.shape

@@ -1,0 +1,214 @@
+"""Thin ctypes binding of the lbmrv C ABI (include/lbmrv.h).
+
+Each ``lbmrv_*`` function here has the name, arguments and meaning of the C entry
+point; this module only marshals arguments (torch tensors become device or host
+pointers, CUDA streams become handles) and turns negative status codes into
+``LbmrvError``. All computation runs in the CUDA library; there is no Python or CPU
+fallback, and importing fails loudly when the library cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+from . import build as _build
+
+LBMRV_OK = 0
+LBMRV_E_INVAL = -1
+LBMRV_E_CUDA = -2
+LBMRV_E_NOMEM = -3
+LBMRV_E_NONFINITE = -4
+LBMRV_E_TIMEOUT = -5
+LBMRV_E_UNSUPPORTED = -6
+
+LBMRV_D2Q9 = 0
+LBMRV_D3Q19 = 1
+LBMRV_UT_ZERO = 0
+LBMRV_UT_FLUID = 1
+LBMRV_UT_PRESCRIBED = 2
+LBMRV_FP32 = 0
+LBMRV_FP16 = 1
+LBMRV_BF16 = 2
+
+_STATUS_NAMES = {
+    LBMRV_E_INVAL: "LBMRV_E_INVAL", LBMRV_E_CUDA: "LBMRV_E_CUDA",
+    LBMRV_E_NOMEM: "LBMRV_E_NOMEM", LBMRV_E_NONFINITE: "LBMRV_E_NONFINITE",
+    LBMRV_E_TIMEOUT: "LBMRV_E_TIMEOUT", LBMRV_E_UNSUPPORTED: "LBMRV_E_UNSUPPORTED",
+}
+
+# (name, restype, argtypes) of every exported entry point.
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+_DP = ctypes.POINTER(ctypes.c_double)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("lbmrv_version", _I, []),
+    ("lbmrv_state_bytes", _I64, [_I, _I64P, _I]),
+    ("lbmrv_create", _I, [ctypes.POINTER(_VP), _I, _I64P, _D, _DP, _I, _I, _D, _VP, _VP, _VP]),
+    ("lbmrv_destroy", _I, [_VP]),
+    ("lbmrv_last_error", ctypes.c_char_p, [_VP]),
+    ("lbmrv_set_stream", _I, [_VP, _VP]),
+    ("lbmrv_set_kernel_width", _I, [_VP, _I]),
+    ("lbmrv_set_utilde", _I, [_VP, _VP, _D, _D]),
+    ("lbmrv_init_equilibrium", _I, [_VP, _VP, _VP]),
+    ("lbmrv_init_equilibrium_host", _I, [_VP, _VP, _VP]),
+    ("lbmrv_step", _I, [_VP, _I64]),
+    ("lbmrv_moments", _I, [_VP, _VP, _VP]),
+    ("lbmrv_moments_host", _I, [_VP, _VP, _VP]),
+    ("lbmrv_conserved", _I, [_VP, _DP]),
+    ("lbmrv_get_state", _I, [_VP, _VP]),
+    ("lbmrv_set_state", _I, [_VP, _VP, _I64]),
+    ("lbmrv_state_ptr", _I, [_VP, ctypes.POINTER(_VP)]),
+    ("lbmrv_time", _I64, [_VP]),
+]
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LbmrvError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load liblbmrv.so (building it first when stale). Raises if it cannot."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_needed else _build.LIB_PATH
+            lib = ctypes.CDLL(path)
+            for name, res, args in SIGNATURES:
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _err(h) -> str:
+    msg = load().lbmrv_last_error(h)
+    return msg.decode() if msg else ""
+
+
+def _check(rc: int, h=None) -> int:
+    if rc < 0:
+        raise LbmrvError(rc, _err(h))
+    return rc
+
+
+def _addr(x) -> int | None:
+    """Pointer of a torch tensor (or an int address / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if not x.is_contiguous():
+        raise ValueError("lbmrv needs contiguous tensors")
+    return x.data_ptr()
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s or None
+    return s.cuda_stream or None
+
+
+def _dims(dims) -> ctypes.Array:
+    d = list(dims) + [1] * (3 - len(dims))
+    return (ctypes.c_int64 * 3)(*d)
+
+
+# ------------------------------------------------------------------ entry points
+def lbmrv_version() -> int:
+    return load().lbmrv_version()
+
+
+def lbmrv_state_bytes(lattice: int, dims, storage: int) -> int:
+    return load().lbmrv_state_bytes(lattice, _dims(dims), storage)
+
+
+def lbmrv_create(lattice: int, dims, lam: float, s, umode: int, storage: int,
+                 rho_ref: float, stream=None, f_a=None, f_b=None) -> int:
+    h = _VP()
+    sv = (ctypes.c_double * 9)(*[float(v) for v in s])
+    rc = load().lbmrv_create(ctypes.byref(h), lattice, _dims(dims), float(lam), sv, umode,
+                             storage, float(rho_ref), _stream(stream), _addr(f_a), _addr(f_b))
+    _check(rc, None)
+    return h.value
+
+
+def lbmrv_destroy(h) -> None:
+    _check(load().lbmrv_destroy(h), None)
+
+
+def lbmrv_last_error(h) -> str:
+    return _err(h)
+
+
+def lbmrv_set_stream(h, stream) -> None:
+    _check(load().lbmrv_set_stream(h, _stream(stream)), h)
+
+
+def lbmrv_set_kernel_width(h, nodes_per_thread: int) -> None:
+    _check(load().lbmrv_set_kernel_width(h, int(nodes_per_thread)), h)
+
+
+def lbmrv_set_utilde(h, ut0, amplitude: float, period: float) -> None:
+    _check(load().lbmrv_set_utilde(h, _addr(ut0), float(amplitude), float(period)), h)
+
+
+def lbmrv_init_equilibrium(h, rho, u) -> None:
+    _check(load().lbmrv_init_equilibrium(h, _addr(rho), _addr(u)), h)
+
+
+def lbmrv_init_equilibrium_host(h, rho, u) -> None:
+    _check(load().lbmrv_init_equilibrium_host(h, _addr(rho), _addr(u)), h)
+
+
+def lbmrv_step(h, n: int) -> None:
+    _check(load().lbmrv_step(h, int(n)), h)
+
+
+def lbmrv_moments(h, rho, u) -> None:
+    _check(load().lbmrv_moments(h, _addr(rho), _addr(u)), h)
+
+
+def lbmrv_moments_host(h, rho, u) -> None:
+    _check(load().lbmrv_moments_host(h, _addr(rho), _addr(u)), h)
+
+
+def lbmrv_conserved(h, allow_nonfinite: bool = False):
+    out = (ctypes.c_double * 4)()
+    rc = load().lbmrv_conserved(h, out)
+    if rc == LBMRV_E_NONFINITE and allow_nonfinite:
+        return list(out)
+    _check(rc, h)
+    return list(out)
+
+
+def lbmrv_get_state(h, dst) -> None:
+    _check(load().lbmrv_get_state(h, _addr(dst)), h)
+
+
+def lbmrv_set_state(h, src, t: int) -> None:
+    _check(load().lbmrv_set_state(h, _addr(src), int(t)), h)
+
+
+def lbmrv_state_ptr(h) -> int:
+    p = _VP()
+    _check(load().lbmrv_state_ptr(h, ctypes.byref(p)), h)
+    return p.value
+
+
+def lbmrv_time(h) -> int:
+    return load().lbmrv_time(h)

@@ -1,0 +1,400 @@
+// D2Q9 kernels: fused pull-transport + relative-velocity relaxation, equilibrium
+// initialisation, moments and FP64 conserved-quantity reductions.
+#include <cuda_runtime.h>
+
+#include "d2q9.cuh"
+#include "launch.h"
+
+namespace lbmrv {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// --------------------------------------------------------------------------------------
+// Fused step, one node per thread. Works for every lattice size (ragged rows, nx or
+// ny equal to 1 or 2). Relation (transport) in pull form: node (x, y) reads population
+// j from (x - cx_j, y - cy_j), periodic.
+template <typename T, int UM>
+__global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
+                                                     T* __restrict__ dst, StepArgs a) {
+    const int nx = a.nx, ny = a.ny;
+    const int64_t n = (int64_t)nx * ny;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nx) return;
+    const int xm = x == 0 ? nx - 1 : x - 1;
+    const int xp = x == nx - 1 ? 0 : x + 1;
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const int ym = y == 0 ? ny - 1 : y - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1;
+        const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+        float g[9];
+        g[0] = to_f(src[r0 + x]);
+        g[1] = to_f(src[n + r0 + xm]);
+        g[2] = to_f(src[2 * n + rm + x]);
+        g[3] = to_f(src[3 * n + r0 + xp]);
+        g[4] = to_f(src[4 * n + rp + x]);
+        g[5] = to_f(src[5 * n + rm + xm]);
+        g[6] = to_f(src[6 * n + rm + xp]);
+        g[7] = to_f(src[7 * n + rp + xp]);
+        g[8] = to_f(src[8 * n + rp + xm]);
+        float ux, uy;
+        relative_velocity<UM>(g, a.rho_ref, x, y, r0 + x, a, ux, uy);
+        relax_node(g, ux, uy, a.s, a.rho_ref);
+#pragma unroll
+        for (int j = 0; j < 9; ++j) dst[j * n + r0 + x] = from_f<T>(g[j]);
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// Fused step, NV consecutive nodes of a row per thread with aligned vector loads and
+// stores (requires nx % NV == 0 and 16-byte aligned planes). Populations moving along
+// +x / -x need the element one before / after the thread's aligned pack: it comes from
+// the neighbouring lane by a warp shuffle, and the lanes at a warp or row edge load it
+// directly (with the periodic wrap).
+template <typename T, int NV>
+struct alignas(sizeof(T) * NV) Pack {
+    T v[NV];
+};
+
+template <typename T, int NV>
+__device__ __forceinline__ void load_pack(const T* __restrict__ p, bool act, float out[NV]) {
+    if (act) {
+        const Pack<T, NV> pk = *reinterpret_cast<const Pack<T, NV>*>(p);
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = to_f(pk.v[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) out[k] = 0.0f;
+    }
+}
+
+// Row segment pulled from x - 1: (prev, v0, ..., v_{NV-2}).
+template <typename T, int NV>
+__device__ __forceinline__ void load_from_left(const T* __restrict__ row, int x0, int xprev,
+                                               bool act, bool edge, float out[NV]) {
+    float v[NV];
+    load_pack<T, NV>(row + x0, act, v);
+    float prev = __shfl_up_sync(FULL, v[NV - 1], 1);
+    if (edge && act) prev = to_f(row[xprev]);
+    out[0] = prev;
+#pragma unroll
+    for (int k = 1; k < NV; ++k) out[k] = v[k - 1];
+}
+
+// Row segment pulled from x + 1: (v1, ..., v_{NV-1}, next).
+template <typename T, int NV>
+__device__ __forceinline__ void load_from_right(const T* __restrict__ row, int x0, int xnext,
+                                                bool act, bool edge, float out[NV]) {
+    float v[NV];
+    load_pack<T, NV>(row + x0, act, v);
+    float next = __shfl_down_sync(FULL, v[0], 1);
+    if (edge && act) next = to_f(row[xnext]);
+#pragma unroll
+    for (int k = 0; k < NV - 1; ++k) out[k] = v[k + 1];
+    out[NV - 1] = next;
+}
+
+template <typename T, int NV, int UM>
+__global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
+                                                  T* __restrict__ dst, StepArgs a) {
+    const int nx = a.nx, ny = a.ny;
+    const int64_t n = (int64_t)nx * ny;
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * NV;
+    const bool act = x0 < nx;
+    const bool left_edge = lane == 0;  // lane - 1 exists and is active otherwise
+    const bool right_edge = lane == 31 || x0 + NV >= nx;
+    const int xprev = x0 == 0 ? nx - 1 : x0 - 1;
+    const int xnext = x0 + NV >= nx ? 0 : x0 + NV;
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const int ym = y == 0 ? ny - 1 : y - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1;
+        const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+        float g[9][NV];
+        load_pack<T, NV>(src + r0 + x0, act, g[0]);
+        load_from_left<T, NV>(src + n + r0, x0, xprev, act, left_edge, g[1]);
+        load_pack<T, NV>(src + 2 * n + rm + x0, act, g[2]);
+        load_from_right<T, NV>(src + 3 * n + r0, x0, xnext, act, right_edge, g[3]);
+        load_pack<T, NV>(src + 4 * n + rp + x0, act, g[4]);
+        load_from_left<T, NV>(src + 5 * n + rm, x0, xprev, act, left_edge, g[5]);
+        load_from_right<T, NV>(src + 6 * n + rm, x0, xnext, act, right_edge, g[6]);
+        load_from_right<T, NV>(src + 7 * n + rp, x0, xnext, act, right_edge, g[7]);
+        load_from_left<T, NV>(src + 8 * n + rp, x0, xprev, act, left_edge, g[8]);
+        if (act) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                float h[9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) h[j] = g[j][k];
+                float ux, uy;
+                relative_velocity<UM>(h, a.rho_ref, x0 + k, y, r0 + x0 + k, a, ux, uy);
+                relax_node(h, ux, uy, a.s, a.rho_ref);
+#pragma unroll
+                for (int j = 0; j < 9; ++j) g[j][k] = h[j];
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                Pack<T, NV> pk;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) pk.v[k] = from_f<T>(g[j][k]);
+                *reinterpret_cast<Pack<T, NV>*>(dst + j * n + r0 + x0) = pk;
+            }
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// Equilibrium initialisation: g_j = f_eq,j(rho, u) - w_j rho_ref, written as
+// w_j (rho - rho_ref) + w_j rho (3 c.u + 9/2 (c.u)^2 - 3/2 |u|^2) with u in units of lambda.
+__constant__ int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+template <typename T>
+__global__ void k_init_eq(T* __restrict__ dst, const float* __restrict__ rho,
+                          const float* __restrict__ u, int64_t n, float rho_ref,
+                          float inv_lambda) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float r = rho ? rho[i] : 1.0f;
+        const float ux = u ? u[i] * inv_lambda : 0.0f;
+        const float uy = u ? u[n + i] * inv_lambda : 0.0f;
+        const float uu = ux * ux + uy * uy;
+        const float dr = r - rho_ref;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const float cu = (float)kCX[j] * ux + (float)kCY[j] * uy;
+            const float w = wgt(j);
+            dst[j * n + i] = from_f<T>(w * dr + w * r * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+        }
+    }
+}
+
+// Density and velocity (relation (rhoq)) of the stored state.
+template <typename T>
+__global__ void k_moments(const T* __restrict__ src, float* __restrict__ rho,
+                          float* __restrict__ u, int64_t n, float rho_ref, float lambda) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float g[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * n + i]);
+        const NodeMoments m = node_moments(g);
+        const float r = rho_ref + m.drho;
+        if (rho) rho[i] = r;
+        if (u) {
+            u[i] = lambda * m.jx / r;
+            u[n + i] = lambda * m.jy / r;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------------------
+// FP64 sums of (rho - rho_ref, q_x / lambda, q_y / lambda, non-finite nodes): per-node
+// FP32 moments accumulated in FP64 per thread, warp-shuffle and shared-memory tree per
+// block, one partial per block; a second one-block kernel adds the partials in a fixed
+// order, so the result is deterministic.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum4(double v[4], double* out) {
+    __shared__ double sh[NT / 32][4];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        v[c] = warp_sum(v[c]);
+        if (l == 0) sh[w][c] = v[c];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double t = l < NT / 32 ? sh[l][c] : 0.0;
+            t = warp_sum(t);
+            if (l == 0) out[c] = t;
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* __restrict__ src,
+                                                                      int64_t n,
+                                                                      double* __restrict__ part) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float g[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * n + i]);
+        const NodeMoments m = node_moments(g);
+        v[0] += (double)m.drho;
+        v[1] += (double)m.jx;
+        v[2] += (double)m.jy;
+        v[3] += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy)) ? 0.0 : 1.0;
+    }
+    block_sum4<kReduceThreads>(v, part + 4 * (int64_t)blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kReduceThreads) k_conserved_final(const double* __restrict__ part,
+                                                                    int nblk, double rho_ref_n,
+                                                                    double lambda,
+                                                                    double* __restrict__ out) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] += part[4 * b + c];
+    }
+    __shared__ double res[4];
+    block_sum4<kReduceThreads>(v, res);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        out[0] = res[0] + rho_ref_n;
+        out[1] = lambda * res[1];
+        out[2] = lambda * res[2];
+        out[3] = res[3];
+    }
+}
+
+int grid_for(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = 152LL * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <typename T, int UM>
+cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
+                             int nv) {
+    const T* s = static_cast<const T*>(src);
+    T* d = static_cast<T*>(dst);
+    const int gy = a.ny < 65535 ? a.ny : 65535;
+    if (nv == 1) {
+        dim3 grid((a.nx + 255) / 256, gy);
+        k_step_scalar<T, UM><<<grid, 256, 0, st>>>(s, d, a);
+    } else if (nv == 2) {
+        dim3 grid(((a.nx / 2) + 127) / 128, gy);
+        k_step_vec<T, 2, UM><<<grid, 128, 0, st>>>(s, d, a);
+    } else if (nv == 4) {
+        dim3 grid(((a.nx / 4) + 127) / 128, gy);
+        k_step_vec<T, 4, UM><<<grid, 128, 0, st>>>(s, d, a);
+    } else if (nv == 8) {
+        if constexpr (sizeof(T) == 2) {
+            dim3 grid(((a.nx / 8) + 127) / 128, gy);
+            k_step_vec<T, 8, UM><<<grid, 128, 0, st>>>(s, d, a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t step_dispatch_um(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
+                             int um, int nv) {
+    switch (um) {
+        case UM_ZERO: return step_dispatch_nv<T, UM_ZERO>(src, dst, a, st, nv);
+        case UM_FLUID: return step_dispatch_nv<T, UM_FLUID>(src, dst, a, st, nv);
+        case UM_ANALYTIC: return step_dispatch_nv<T, UM_ANALYTIC>(src, dst, a, st, nv);
+        case UM_FIELD: return step_dispatch_nv<T, UM_FIELD>(src, dst, a, st, nv);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int step_vector_width(int storage, int nx) {
+    // Widest pack that divides nx: 16-byte packs for FP32 (4) and 2-byte types (8).
+    const int widest = storage == kStoreF32 ? 4 : 8;
+    for (int nv = widest; nv > 1; nv >>= 1)
+        if (nx % nv == 0 && nx >= nv) return nv;
+    return 1;
+}
+
+cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
+                        const StepArgs& a, cudaStream_t st) {
+    switch (storage) {
+        case kStoreF32: return step_dispatch_um<float>(src, dst, a, st, um, nv);
+        case kStoreF16: return step_dispatch_um<__half>(src, dst, a, st, um, nv);
+        case kStoreBF16: return step_dispatch_um<__nv_bfloat16>(src, dst, a, st, um, nv);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
+                           float rho_ref, float inv_lambda, cudaStream_t st) {
+    const int g = grid_for(n, 256);
+    switch (storage) {
+        case kStoreF32:
+            k_init_eq<float><<<g, 256, 0, st>>>(static_cast<float*>(dst), rho, u, n, rho_ref,
+                                                inv_lambda);
+            break;
+        case kStoreF16:
+            k_init_eq<__half><<<g, 256, 0, st>>>(static_cast<__half*>(dst), rho, u, n, rho_ref,
+                                                 inv_lambda);
+            break;
+        case kStoreBF16:
+            k_init_eq<__nv_bfloat16><<<g, 256, 0, st>>>(static_cast<__nv_bfloat16*>(dst), rho, u,
+                                                        n, rho_ref, inv_lambda);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, int64_t n,
+                           float rho_ref, float lambda, cudaStream_t st) {
+    const int g = grid_for(n, 256);
+    switch (storage) {
+        case kStoreF32:
+            k_moments<float><<<g, 256, 0, st>>>(static_cast<const float*>(src), rho, u, n,
+                                                rho_ref, lambda);
+            break;
+        case kStoreF16:
+            k_moments<__half><<<g, 256, 0, st>>>(static_cast<const __half*>(src), rho, u, n,
+                                                 rho_ref, lambda);
+            break;
+        case kStoreBF16:
+            k_moments<__nv_bfloat16><<<g, 256, 0, st>>>(
+                static_cast<const __nv_bfloat16*>(src), rho, u, n, rho_ref, lambda);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int conserved_blocks(int64_t n) {
+    int64_t b = (n + kReduceThreads - 1) / kReduceThreads;
+    return (int)(b < 1 ? 1 : (b > kReduceMaxBlocks ? kReduceMaxBlocks : b));
+}
+
+cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho_ref,
+                             double lambda, double* partials, int nblk, double* out,
+                             cudaStream_t st) {
+    switch (storage) {
+        case kStoreF32:
+            k_conserved_partial<float><<<nblk, kReduceThreads, 0, st>>>(
+                static_cast<const float*>(src), n, partials);
+            break;
+        case kStoreF16:
+            k_conserved_partial<__half><<<nblk, kReduceThreads, 0, st>>>(
+                static_cast<const __half*>(src), n, partials);
+            break;
+        case kStoreBF16:
+            k_conserved_partial<__nv_bfloat16><<<nblk, kReduceThreads, 0, st>>>(
+                static_cast<const __nv_bfloat16*>(src), n, partials);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_conserved_final<<<1, kReduceThreads, 0, st>>>(partials, nblk, rho_ref * (double)n, lambda,
+                                                    out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmrv

@@ -1,0 +1,138 @@
+"""Convenience wrapper around one lbmrv handle, with PyTorch owning the device memory.
+
+``D2Q9`` allocates the two population buffers as torch tensors on the current CUDA
+device, enqueues on torch's current stream, and forwards every operation to the C
+entry points of ``binding``. It does no arithmetic of its own.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import binding as B
+
+_MODES = {"zero": B.LBMRV_UT_ZERO, "fluid": B.LBMRV_UT_FLUID,
+          "prescribed": B.LBMRV_UT_PRESCRIBED}
+_STORAGES = {"fp32": B.LBMRV_FP32, "fp16": B.LBMRV_FP16, "bf16": B.LBMRV_BF16}
+STORAGE_DTYPES = {B.LBMRV_FP32: torch.float32, B.LBMRV_FP16: torch.float16,
+                  B.LBMRV_BF16: torch.bfloat16}
+WEIGHTS = (4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 36, 1 / 36)
+
+
+def mode_id(mode) -> int:
+    return _MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+def storage_id(storage) -> int:
+    return _STORAGES[storage] if isinstance(storage, str) else int(storage)
+
+
+class D2Q9:
+    """A periodic nx x ny D2Q9 lattice advanced by the relative-velocity scheme."""
+
+    def __init__(self, nx: int, ny: int, s, mode="fluid", storage="fp32", lam: float = 1.0,
+                 rho_ref: float | None = None, device=None, stream=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.n = self.nx * self.ny
+        self.mode = mode_id(mode)
+        self.storage = storage_id(storage)
+        self.lam = float(lam)
+        if rho_ref is None:
+            rho_ref = 1.0  # store deviations from the rest state: smaller rounding error
+        self.rho_ref = float(rho_ref)
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        nbytes = B.lbmrv_state_bytes(B.LBMRV_D2Q9, (self.nx, self.ny, 1), self.storage)
+        if nbytes <= 0:
+            raise ValueError(f"invalid lattice {nx} x {ny}")
+        self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+                      for _ in range(2)]
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        with torch.cuda.device(self.device):
+            self.h = B.lbmrv_create(B.LBMRV_D2Q9, (self.nx, self.ny, 1), self.lam, list(s),
+                                    self.mode, self.storage, self.rho_ref, self.stream,
+                                    self._bufs[0], self._bufs[1])
+        self._ut0 = None
+        self.dtype = STORAGE_DTYPES[self.storage]
+
+    # -- lifecycle
+    def close(self):
+        if getattr(self, "h", None):
+            B.lbmrv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- configuration
+    def set_kernel_width(self, nodes_per_thread: int):
+        B.lbmrv_set_kernel_width(self.h, nodes_per_thread)
+
+    def set_utilde(self, ut0=None, amplitude: float = 0.0, period: float = 0.0):
+        if ut0 is not None:
+            ut0 = torch.as_tensor(ut0, dtype=torch.float32, device=self.device).contiguous()
+            if ut0.numel() != 2 * self.n:
+                raise ValueError("u~0 must hold 2 * nx * ny values")
+        self._ut0 = ut0  # keep the field alive while the handle refers to it
+        B.lbmrv_set_utilde(self.h, ut0, amplitude, period)
+
+    # -- state
+    def init_equilibrium(self, rho, ux, uy):
+        rho = torch.as_tensor(rho, dtype=torch.float32, device=self.device).contiguous()
+        u = torch.stack([torch.as_tensor(ux, dtype=torch.float32, device=self.device),
+                         torch.as_tensor(uy, dtype=torch.float32, device=self.device)])
+        u = u.contiguous()
+        B.lbmrv_init_equilibrium(self.h, rho, u)
+        self._keep = (rho, u)  # the copy is asynchronous on the stream
+
+    def init_equilibrium_host(self, rho_host, u_host):
+        """rho_host: CPU float32 [n] (pinned for speed); u_host: CPU float32 [2, n]."""
+        B.lbmrv_init_equilibrium_host(self.h, rho_host, u_host)
+
+    def step(self, n: int = 1):
+        B.lbmrv_step(self.h, n)
+
+    @property
+    def time(self) -> int:
+        return B.lbmrv_time(self.h)
+
+    def moments(self):
+        rho = torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device)
+        u = torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        B.lbmrv_moments(self.h, rho, u)
+        return rho, u[0], u[1]
+
+    def moments_host(self, rho_host=None, u_host=None):
+        if rho_host is None:
+            rho_host = torch.empty((self.ny, self.nx), dtype=torch.float32, pin_memory=True)
+        if u_host is None:
+            u_host = torch.empty((2, self.ny, self.nx), dtype=torch.float32, pin_memory=True)
+        B.lbmrv_moments_host(self.h, rho_host, u_host)
+        return rho_host, u_host
+
+    def conserved(self, allow_nonfinite: bool = False):
+        return B.lbmrv_conserved(self.h, allow_nonfinite=allow_nonfinite)
+
+    def state(self) -> torch.Tensor:
+        """Copy of the stored state g = f - w rho_ref, shape (9, ny, nx), storage dtype."""
+        out = torch.empty((9, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        B.lbmrv_get_state(self.h, out)
+        return out
+
+    def set_state(self, g: torch.Tensor, t: int = 0):
+        g = g.to(device=self.device, dtype=self.dtype).contiguous()
+        if g.numel() != 9 * self.n:
+            raise ValueError("state must hold 9 * nx * ny values")
+        B.lbmrv_set_state(self.h, g, t)
+        self._keep = g
+
+    def state_ptr(self) -> int:
+        return B.lbmrv_state_ptr(self.h)

@@ -1,0 +1,62 @@
+"""Helpers that run the CUDA path and the oracle on the same seeded inputs and measure
+their difference. Test infrastructure: imports both sides, which never import each other."""
+from __future__ import annotations
+
+import numpy as np
+
+import lbm_inputs as inp
+
+S_PAPER = [0, 0, 0, 1.4, 1.9, 1.9, 1.2, 1.2, 1.4]
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+MODES = {"zero": 0, "fluid": 1, "prescribed": 2}
+
+
+def f32_fields(d):
+    return tuple(inp.to_f32_exact(d[k]) for k in ("rho", "ux", "uy"))
+
+
+def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=None,
+            ut0=None, amp=0.0, period=0.0, width=0):
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9
+
+    rho, ux, uy = fields
+    sim = D2Q9(nx, ny, s, mode=mode, storage=storage, lam=lam, rho_ref=rho_ref)
+    if width:
+        sim.set_kernel_width(width)
+    if MODES[mode] == 2:
+        sim.set_utilde(None if ut0 is None else torch.as_tensor(ut0, dtype=torch.float32),
+                       amp, period)
+    sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+    sim.step(steps)
+    g = sim.state().double().cpu().numpy()
+    f = g + W[:, None, None] * sim.rho_ref
+    r, a, b = (t.double().cpu().numpy() for t in sim.moments())
+    sim.close()
+    return f, (r, a, b)
+
+
+def oracle_run(nx, ny, s, mode, steps, fields, lam=1.0, ut0=None, amp=0.0, period=0.0,
+               method=0, nthreads=8):
+    import oracle
+
+    rho, ux, uy = fields
+    f0 = oracle.init_equilibrium(rho, ux, uy, lam)
+    ut = None if ut0 is None else inp.to_f32_exact(ut0)
+    S = oracle.post_collision_state(f0, lam, np.asarray(s, float), MODES[mode], steps,
+                                    ut0=ut, amp=amp, period=period, method=method,
+                                    nthreads=nthreads)
+    return S, oracle.moments(S, lam)
+
+
+def rel_errors(f_g, m_g, f_o, m_o):
+    """rho: max|drho| / max|rho|; u: max_x |du(x)|_2 / max_x |u(x)|_2;
+    f: max|df| / max|f|."""
+    r_g, ux_g, uy_g = m_g
+    r_o, ux_o, uy_o = m_o
+    e_rho = np.abs(r_g - r_o).max() / np.abs(r_o).max()
+    du = np.hypot(ux_g - ux_o, uy_g - uy_o).max()
+    e_u = du / max(np.hypot(ux_o, uy_o).max(), 1e-300)
+    e_f = np.abs(f_g - f_o).max() / np.abs(f_o).max()
+    return e_rho, e_u, e_f
