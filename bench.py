@@ -199,9 +199,10 @@ def gpu_arm(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     binding.load()
     peak, peak_kind = measured_peaks()
-    n = L * L
-    fields = inp.taylor_green(L, L, u0=0.04)
-    sim = make_sim(torch, D2Q9, inp, "fp32", "prescribed", L, fields)
+    size = args.size
+    n = size * size
+    fields = inp.taylor_green(size, size, u0=0.04)
+    sim = make_sim(torch, D2Q9, inp, "fp32", "prescribed", size, fields)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
@@ -233,7 +234,7 @@ def gpu_arm(args):
     out = None
     if rank == 0:
         extras = {}
-        if not args.no_extras and world == 1:
+        if not args.no_extras and world == 1 and size == L:
             k = max(50, min(args.steps, 300))
             extras["plain_mrt_u0"] = side_measure(torch, D2Q9, inp, "fp32", "zero", L, fields,
                                                   k, peak)
@@ -250,14 +251,15 @@ def gpu_arm(args):
             extras["fp32_fluid_8192"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", 8192,
                                                      big, k, peak)
             del big
-        e2e = e2e_measure(torch, D2Q9, inp, fields, args.steps) if not args.no_e2e else None
+        e2e = (e2e_measure(torch, D2Q9, inp, fields, args.steps)
+               if not args.no_e2e and size == L else None)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
         out = {
             "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_ms, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nodes": n, "bytes_per_node_step": 72,
+            "config": {"workload": WORKLOAD.replace("4096x4096", f"{size}x{size}"), "nodes": n, "bytes_per_node_step": 72,
                        "l2": "state 1.2 GB > 129 MB L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
@@ -402,6 +404,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=L,
+                    help="lattice side (a smaller case for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
