@@ -179,6 +179,28 @@ LBMRV_API int lbmrv_state_ptr(lbmrv_t h, void** ptr_out);
 /* Time index of the current state (number of steps since the last init/set_state). */
 LBMRV_API int64_t lbmrv_time(lbmrv_t h);
 
+/* The same sums as lbmrv_conserved for a caller-owned D2Q9 state, with no handle and no
+ * device allocation. The paper has no counterpart: this exists for callers that cannot
+ * allocate when they need the check (an allocator that owns all device memory, a loop
+ * where cudaMalloc would synchronise the device, a monitor of a buffer it did not
+ * create). Scratch comes from a fixed 38,912-byte array in the library's device image,
+ * present on every GPU that loads the library until the process exits.
+ *   state_dev  device state in the layout above (9 planes of nx*ny, storage type).
+ *   storage    LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16; rho_ref the stored offset.
+ *   dims       {nx, ny, 1}; nx*ny must be below 2^31 (larger sizes: LBMRV_E_INVAL).
+ *   out_dev    4 device doubles: sum rho, sum q_x, sum q_y, non-finite node count.
+ *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * Asynchronous; allocates nothing (no cudaMalloc, no cudaFree). The first call on a
+ * device looks up the scratch array's device address (cudaGetSymbolAddress), so make
+ * that first call before any stream capture. Every call shares the one scratch array:
+ * calls that overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller. Each call overwrites all the scratch it reads, so nothing
+ * needs clearing. Returns LBMRV_OK, LBMRV_E_INVAL or LBMRV_E_CUDA (no message is kept,
+ * as there is no handle). */
+LBMRV_API int lbmrv_conserved_noalloc(const void* state_dev, int storage, const int64_t dims[3],
+                                      double lambda, double rho_ref, double* out_dev,
+                                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("lbmrv_set_state", _I, [_VP, _VP, _I64]),
     ("lbmrv_state_ptr", _I, [_VP, ctypes.POINTER(_VP)]),
     ("lbmrv_time", _I64, [_VP]),
+    ("lbmrv_conserved_noalloc", _I, [_VP, _I, _I64P, _D, _D, _VP, _VP]),
 ]
 
 _lock = threading.Lock()
@@ -212,3 +213,12 @@ def lbmrv_state_ptr(h) -> int:
 
 def lbmrv_time(h) -> int:
     return load().lbmrv_time(h)
+
+
+def lbmrv_conserved_noalloc(state, storage: int, dims, lam: float, rho_ref: float, out,
+                            stream=None) -> None:
+    """Sums of a caller-owned state into ``out`` (4 device doubles) without allocating."""
+    rc = load().lbmrv_conserved_noalloc(_addr(state), int(storage), _dims(dims), float(lam),
+                                        float(rho_ref), _addr(out), _stream(stream))
+    if rc < 0:
+        raise LbmrvError(rc, "lbmrv_conserved_noalloc failed")
