@@ -251,6 +251,7 @@ def gpu_arm(args):
             extras["fp32_fluid_8192"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", 8192,
                                                      big, k, peak)
             del big
+            extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
         e2e = (e2e_measure(torch, D2Q9, inp, fields, args.steps)
                if not args.no_e2e and size == L else None)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
@@ -279,6 +280,70 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
+    """Adjoint workload: 1024^2 noisy shear wave, prescribed u~, kinetic-energy loss,
+    2000 steps with sqrt(N) = 45 checkpoints. Reports the forward step, the adjoint step
+    alone (checkpoint every state on a 200-step window: no recompute), and the whole
+    gradient (checkpointed forward + recompute + reverse sweep + equilibrium adjoint)."""
+    size = 1024
+    n = size * size
+    d = inp.noisy_shear_wave(size, size, seed=0)
+    sim = D2Q9(size, size, S_RATES, mode="prescribed")
+    sim.set_utilde(None, UT_AMP, UT_PERIOD)
+    rho = torch.as_tensor(d["rho"], dtype=torch.float32, device="cuda")
+    u = torch.stack([torch.as_tensor(d[k], dtype=torch.float32, device="cuda")
+                     for k in ("ux", "uy")])
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    st = sim.stream
+    # forward step alone
+    sim.init_equilibrium(rho, u[0], u[1])
+    sim.step(5)
+    fwd_ms = time_steps(sim, 400, torch) / 400
+    # adjoint step alone: every state checkpointed, so the sweep has no recompute
+    w = 200
+    ws = sim.adjoint_workspace(w, 1)
+    sim.init_equilibrium(rho, u[0], u[1])
+    sim.forward_checkpointed(w, 1, ws)
+    _, dlds = sim.kinetic_energy(grad=True)
+    sim.adjoint(w, 1, ws, dlds)  # warm
+    a, b = ev(), ev()
+    a.record(st)
+    sim.adjoint(w, 1, ws, dlds)
+    b.record(st)
+    b.synchronize()
+    adj_ms = a.elapsed_time(b) / w
+    del ws
+    # whole gradient, sqrt(N) checkpoints
+    seg = 45
+    ws = sim.adjoint_workspace(n_steps, seg)
+    torch.cuda.synchronize()
+    e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+    e0.record(st)
+    sim.init_equilibrium(rho, u[0], u[1])
+    sim.forward_checkpointed(n_steps, seg, ws)
+    e1.record(st)
+    ke, dlds = sim.kinetic_energy(grad=True)
+    e2.record(st)
+    d0, ds, da, _ = sim.adjoint(n_steps, seg, ws, dlds)
+    sim.equilibrium_vjp(rho, u, d0)
+    e3.record(st)
+    e3.synchronize()
+    sim.close()
+    ws_gb = ws.numel() / 1e9
+    del ws
+    return {"workload": "1024^2 noisy shear wave, prescribed u~, KE loss, 2000 steps, seg 45",
+            "forward_ms_per_step": round(fwd_ms, 5),
+            "adjoint_ms_per_step": round(adj_ms, 5),
+            "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
+            "adjoint_gbs": round(108 * n / (adj_ms * 1e-3) / 1e9, 1),
+            "adjoint_frac": round(108 * n / (adj_ms * 1e-3) / 1e9 / peak, 4),
+            "checkpointed_forward_ms": round(e0.elapsed_time(e1), 2),
+            "reverse_sweep_ms": round(e2.elapsed_time(e3), 2),
+            "gradient_over_forward_run": round(e0.elapsed_time(e3) / (fwd_ms * n_steps), 3),
+            "workspace_gb": round(ws_gb, 2), "loss": ke, "dL_dsnu": ds[4] + ds[5],
+            "dL_dA": da}
 
 
 def e2e_measure(torch, D2Q9, inp, fields, steps):

@@ -179,6 +179,64 @@ LBMRV_API int lbmrv_state_ptr(lbmrv_t h, void** ptr_out);
 /* Time index of the current state (number of steps since the last init/set_state). */
 LBMRV_API int64_t lbmrv_time(lbmrv_t h);
 
+/* Replace the 9 relaxation rates (same rules as lbmrv_create); applies to later steps. */
+LBMRV_API int lbmrv_set_rates(lbmrv_t h, const double* s);
+
+/* ---------------------------------------------------------------- discrete adjoint
+ * Not in the paper: the reverse-mode derivative of the step as this library computes it.
+ * With S_k = C_k(P S_{k-1}) (P the pull transport, C_k the relaxation at time k), a loss
+ * L(S_N) has the adjoint recursion
+ *   mu_k = J_{C_k}(P S_{k-1})^T a_k,  a_N = dL/dS_N,  a_k = P^T mu_{k+1},  dL/dS_0 = P^T mu_1,
+ * where P^T is a push (the transpose of the pull). J_C^T is the hand-derived transpose of
+ * the shifted relaxation (moments, equilibrium moments, T(u~), S, T(-u~), M(0)^{-1}),
+ * including the dependence of u~ = q/rho on the populations. Parameter gradients are
+ * summed over nodes and steps in FP64. FP32 storage only (else LBMRV_E_UNSUPPORTED).
+ * Memory: sqrt(N)-style checkpointing. lbmrv_forward_checkpointed stores every seg-th
+ * state; lbmrv_adjoint recomputes each segment from its checkpoint (one extra forward in
+ * total) and walks it backwards. */
+
+/* Bytes of the caller-owned workspace for n steps with checkpoints every seg steps
+ * (1 <= seg <= n): ceil(n/seg) + seg + 1 states of 36 bytes per node, plus
+ * accumulators. -1 on invalid arguments. */
+LBMRV_API int64_t lbmrv_adjoint_workspace_bytes(lbmrv_t h, int64_t n, int64_t seg);
+
+/* Advance n steps from the current state (time t0) like lbmrv_step, storing the states
+ * at t0, t0 + seg, t0 + 2 seg, ... in ws_dev (device, 256-byte aligned, at least
+ * lbmrv_adjoint_workspace_bytes). The handle remembers (n, seg, ws, t0) for lbmrv_adjoint.
+ * Errors: LBMRV_E_INVAL, LBMRV_E_NOMEM (workspace too small), LBMRV_E_UNSUPPORTED. */
+LBMRV_API int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
+                                         size_t ws_bytes);
+
+/* Reverse sweep of the last lbmrv_forward_checkpointed(n, seg, ws_dev) (same arguments).
+ *   dL_dS_dev     device FP32 [9][nx*ny]: dL/dS_N, gradient of the loss with respect to
+ *                 the stored state after the n steps (e.g. from lbmrv_kinetic_energy or
+ *                 lbmrv_moments_vjp). Not modified.
+ *   dL_dS0_dev    device FP32 [9][nx*ny] out: dL/dS_0 (may alias nothing else).
+ *   dL_ds_host    9 doubles out, or NULL: dL/ds_k (0 for the conserved k < 3).
+ *   dL_damp_host  1 double out, or NULL: dL/dA for the prescribed mode (0 otherwise).
+ *   dL_dut0_dev   device FP32 [2][nx*ny] out, or NULL: dL/du~0(x) for the prescribed mode
+ *                 with a caller field or the analytic one (overwritten).
+ * Synchronous (returns host values). The handle's current state is not changed. */
+LBMRV_API int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_bytes,
+                            const float* dL_dS_dev, float* dL_dS0_dev, double* dL_ds_host,
+                            double* dL_damp_host, float* dL_dut0_dev);
+
+/* Kinetic energy L = 1/2 sum_x |q|^2 / rho of the current state (FP64 sum, synchronous)
+ * and, when dL_dS_dev (device FP32 [9][nx*ny]) is not NULL, its gradient dL/dS. */
+LBMRV_API int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev);
+
+/* Adjoint of lbmrv_moments at the current state: dL/dS from dL/drho (device FP32 [nx*ny]
+ * or NULL) and dL/du (device FP32 [2][nx*ny] or NULL). Asynchronous. */
+LBMRV_API int lbmrv_moments_vjp(lbmrv_t h, const float* dL_drho_dev, const float* dL_du_dev,
+                                float* dL_dS_dev);
+
+/* Adjoint of lbmrv_init_equilibrium(rho, u): from dL/dS_0 (device FP32 [9][nx*ny]) to
+ * dL/drho (device FP32 [nx*ny] or NULL) and dL/du (device FP32 [2][nx*ny] or NULL).
+ * rho_dev may be NULL (rho = 1), as in lbmrv_init_equilibrium. Asynchronous. */
+LBMRV_API int lbmrv_equilibrium_vjp(lbmrv_t h, const float* rho_dev, const float* u_dev,
+                                    const float* dL_dS0_dev, float* dL_drho_dev,
+                                    float* dL_du_dev);
+
 /* The same sums as lbmrv_conserved for a caller-owned D2Q9 state, with no handle and no
  * device allocation. The paper has no counterpart: this exists for callers that cannot
  * allocate when they need the check (an allocator that owns all device memory, a loop

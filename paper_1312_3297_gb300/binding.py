@@ -63,6 +63,13 @@ SIGNATURES = [
     ("lbmrv_state_ptr", _I, [_VP, ctypes.POINTER(_VP)]),
     ("lbmrv_time", _I64, [_VP]),
     ("lbmrv_conserved_noalloc", _I, [_VP, _I, _I64P, _D, _D, _VP, _VP]),
+    ("lbmrv_set_rates", _I, [_VP, _DP]),
+    ("lbmrv_adjoint_workspace_bytes", _I64, [_VP, _I64, _I64]),
+    ("lbmrv_forward_checkpointed", _I, [_VP, _I64, _I64, _VP, ctypes.c_size_t]),
+    ("lbmrv_adjoint", _I, [_VP, _I64, _I64, _VP, ctypes.c_size_t, _VP, _VP, _DP, _DP, _VP]),
+    ("lbmrv_kinetic_energy", _I, [_VP, _DP, _VP]),
+    ("lbmrv_moments_vjp", _I, [_VP, _VP, _VP, _VP]),
+    ("lbmrv_equilibrium_vjp", _I, [_VP, _VP, _VP, _VP, _VP, _VP]),
 ]
 
 _lock = threading.Lock()
@@ -222,3 +229,40 @@ def lbmrv_conserved_noalloc(state, storage: int, dims, lam: float, rho_ref: floa
                                         float(rho_ref), _addr(out), _stream(stream))
     if rc < 0:
         raise LbmrvError(rc, "lbmrv_conserved_noalloc failed")
+
+
+def lbmrv_set_rates(h, s) -> None:
+    sv = (ctypes.c_double * 9)(*[float(v) for v in s])
+    _check(load().lbmrv_set_rates(h, sv), h)
+
+
+def lbmrv_adjoint_workspace_bytes(h, n: int, seg: int) -> int:
+    return load().lbmrv_adjoint_workspace_bytes(h, int(n), int(seg))
+
+
+def lbmrv_forward_checkpointed(h, n: int, seg: int, ws, ws_bytes: int) -> None:
+    _check(load().lbmrv_forward_checkpointed(h, int(n), int(seg), _addr(ws), int(ws_bytes)), h)
+
+
+def lbmrv_adjoint(h, n: int, seg: int, ws, ws_bytes: int, dL_dS, dL_dS0, dL_dut0=None):
+    """Returns (dL/ds as 9 floats, dL/dA)."""
+    ds = (ctypes.c_double * 9)()
+    da = ctypes.c_double()
+    _check(load().lbmrv_adjoint(h, int(n), int(seg), _addr(ws), int(ws_bytes), _addr(dL_dS),
+                                _addr(dL_dS0), ds, ctypes.byref(da), _addr(dL_dut0)), h)
+    return list(ds), da.value
+
+
+def lbmrv_kinetic_energy(h, dL_dS=None) -> float:
+    ke = ctypes.c_double()
+    _check(load().lbmrv_kinetic_energy(h, ctypes.byref(ke), _addr(dL_dS)), h)
+    return ke.value
+
+
+def lbmrv_moments_vjp(h, dL_drho, dL_du, dL_dS) -> None:
+    _check(load().lbmrv_moments_vjp(h, _addr(dL_drho), _addr(dL_du), _addr(dL_dS)), h)
+
+
+def lbmrv_equilibrium_vjp(h, rho, u, dL_dS0, dL_drho, dL_du) -> None:
+    _check(load().lbmrv_equilibrium_vjp(h, _addr(rho), _addr(u), _addr(dL_dS0), _addr(dL_drho),
+                                        _addr(dL_du)), h)

@@ -10,6 +10,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#define LBMRV_HD __host__ __device__ __forceinline__
+
 namespace lbmrv {
 
 // Rates on the six non-conserved moments (e, p_xx, p_xy, q_x, q_y, eps).
@@ -26,12 +28,14 @@ struct StepArgs {
     float two_over_nx;   // 2 / nx, 2 / ny for cospi/sinpi of the analytic field
     float two_over_ny;
     const float* ut0;    // prescribed base field [2][n] or nullptr
+    float sin_k[8];      // sin(2 pi k / nx), cos(2 pi k / nx), k < 8: the analytic field
+    float cos_k[8];      // at x0 + k from its value at x0 by angle addition
 };
 
 // Modes of u~ (kernel template parameter).
 enum { UM_ZERO = 0, UM_FLUID = 1, UM_ANALYTIC = 2, UM_FIELD = 3 };
 
-__device__ __forceinline__ float wgt(int j) {
+LBMRV_HD float wgt(int j) {
     return j == 0 ? (4.0f / 9.0f) : (j < 5 ? (1.0f / 9.0f) : (1.0f / 36.0f));
 }
 
@@ -55,7 +59,7 @@ struct NodeMoments {
     float jx, jy;  // q / lambda = sum c f = sum c g
 };
 
-__device__ __forceinline__ NodeMoments node_moments(const float g[9]) {
+LBMRV_HD NodeMoments node_moments(const float g[9]) {
     NodeMoments m;
     const float a = g[5] - g[7], b = g[6] - g[8];
     m.drho = ((g[0] + (g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8])));
@@ -72,7 +76,7 @@ __device__ __forceinline__ NodeMoments node_moments(const float g[9]) {
 // T(u~) acts: identity on (e, p_xx, p_xy) plus C3 (rows q_x, q_y), D3 and D4 (row eps)
 // of Appendix A. Then f* = f - M(0)^{-1} T(-u~) S T(u~) d, where M(0)^{-1} =
 // M(0)^T diag(1/|row|^2) with |row|^2 = 36, 4, 4, 12, 12, 36 on the six moments.
-__device__ __forceinline__ void relax_node(float g[9], float ux, float uy, const Rates& s,
+LBMRV_HD void relax_node(float g[9], float ux, float uy, const Rates& s,
                                            float rho_ref) {
     const NodeMoments mo = node_moments(g);
     const float rho = rho_ref + mo.drho;

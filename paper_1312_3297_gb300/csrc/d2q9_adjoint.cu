@@ -1,0 +1,367 @@
+// Adjoint kernels of the D2Q9 relative-velocity step (FP32 state).
+//
+// Forward, as stored by the library: S_k = C_k(P S_{k-1}), P the pull transport of
+// relation (transport), C_k the relaxation at time k (relax_node). For a loss L(S_N):
+//   mu_k = J_{C_k}(P S_{k-1})^T a_k,   a_N = dL/dS_N,   a_k = P^T mu_{k+1} (k < N),
+//   dL/dS_0 = P^T mu_1,
+// where P^T (a push) is read here as a gather: (P^T mu)_j(x) = mu_j(x + c_j). One launch
+// of k_adjoint_step computes mu_k from S_{k-1} (pulled) and mu_{k+1} (gathered) or dL/dS_N
+// (aligned), adds the node contributions to dL/ds (six non-conserved rates) and to dL/dA
+// (amplitude of a prescribed u~) into per-block FP64 accumulators, and optionally adds
+// alpha_k * dL/du~ to a per-node field gradient.
+#include <cuda_runtime.h>
+
+#include "d2q9.cuh"
+#include "d2q9_adjoint.cuh"
+#include "launch.h"
+#include "pull.cuh"
+
+namespace lbmrv {
+
+namespace {
+
+// Prescribed base field u~0 at node (x, y): analytic (cos 2pi y/ny, sin 2pi x/nx) or a
+// caller field [2][n].
+template <int UM>
+__device__ __forceinline__ void base_field(int x, int y, int64_t i, const StepArgs& a,
+                                           float& bx, float& by) {
+    if (UM == UM_ANALYTIC) {
+        bx = cospif(a.two_over_ny * (float)y);
+        by = sinpif(a.two_over_nx * (float)x);
+    } else if (UM == UM_FIELD) {
+        const int64_t n = (int64_t)a.nx * a.ny;
+        bx = __ldg(a.ut0 + i);
+        by = __ldg(a.ut0 + n + i);
+    } else {
+        bx = 0.0f;
+        by = 0.0f;
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFullMask, v, o);
+    return v;
+}
+
+// Add the block's sums of v[0..6] to acc[block * 8 + c] in FP64 (the block owns its slot).
+template <int NT>
+__device__ __forceinline__ void block_accumulate7(float v[7], double* __restrict__ acc) {
+    __shared__ float sh[NT / 32][7];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+        const float t = warp_sum_f(v[c]);
+        if (l == 0) sh[w][c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) s += (double)sh[k][threadIdx.x];
+        const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+        acc[blk * 8 + threadIdx.x] += s;
+    }
+}
+
+constexpr int kAdjThreads = 128;
+
+template <int NV, int UM, bool GATHER>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __restrict__ s_prev,
+                                                              const float* __restrict__ a_in,
+                                                              float* __restrict__ mu_out,
+                                                              AdjointArgs aa) {
+    const StepArgs& a = aa.step;
+    const int nx = a.nx, ny = a.ny;
+    const int64_t n = (int64_t)nx * ny;
+    const PackLane p = pack_lane<NV>(nx);
+    float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const int ym = y == 0 ? ny - 1 : y - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1;
+        const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+        float g[9][NV], adj[9][NV];
+        pull_pack<float, NV>(s_prev, n, r0, rm, rp, p, g);
+        if (GATHER) {
+            gather_pack<float, NV>(a_in, n, r0, rm, rp, p, adj);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) load_pack<float, NV>(a_in + j * n + r0 + p.x0, p.act, adj[j]);
+        }
+        if (p.act) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                float h[9], ah[9], o[9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    h[j] = g[j][k];
+                    ah[j] = adj[j][k];
+                }
+                const int x = p.x0 + k;
+                const int64_t i = r0 + x;
+                float bx, by, ux, uy;
+                base_field<UM>(x, y, i, a, bx, by);
+                if (UM == UM_FLUID) {
+                    const NodeMoments m = node_moments(h);
+                    const float ir = 1.0f / (a.rho_ref + m.drho);
+                    ux = m.jx * ir;
+                    uy = m.jy * ir;
+                } else {
+                    ux = a.amp_t * bx;
+                    uy = a.amp_t * by;
+                }
+                float ubx, uby;
+                relax_node_vjp<UM>(h, ah, ux, uy, a.s, a.rho_ref, o, acc, ubx, uby);
+                if (UM == UM_ANALYTIC || UM == UM_FIELD) {
+                    acc[6] += aa.da_factor * (ubx * bx + uby * by);
+                    if (aa.dut0) {
+                        aa.dut0[i] += a.amp_t * ubx;
+                        aa.dut0[n + i] += a.amp_t * uby;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 9; ++j) g[j][k] = o[j];
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) store_pack<float, NV>(mu_out + j * n + r0 + p.x0, g[j]);
+        }
+    }
+    block_accumulate7<kAdjThreads>(acc, aa.acc);
+}
+
+// dst = P^T src (gather), used once for dL/dS_0 = P^T mu_1.
+template <int NV>
+__global__ void __launch_bounds__(kAdjThreads) k_gather(const float* __restrict__ src,
+                                                        float* __restrict__ dst, int nx, int ny) {
+    const int64_t n = (int64_t)nx * ny;
+    const PackLane p = pack_lane<NV>(nx);
+    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+        const int ym = y == 0 ? ny - 1 : y - 1;
+        const int yp = y == ny - 1 ? 0 : y + 1;
+        const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+        float v[9][NV];
+        gather_pack<float, NV>(src, n, r0, rm, rp, p, v);
+        if (p.act) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) store_pack<float, NV>(dst + j * n + r0 + p.x0, v[j]);
+        }
+    }
+}
+
+// Sum of the per-block accumulators, fixed order: out[c] = sum_b acc[b * 8 + c].
+__global__ void __launch_bounds__(256) k_acc_final(const double* __restrict__ acc, int64_t nblk,
+                                                   double* __restrict__ out) {
+    __shared__ double sh[256];
+    for (int c = 0; c < 8; ++c) {
+        double s = 0.0;
+        for (int64_t b = threadIdx.x; b < nblk; b += blockDim.x) s += acc[b * 8 + c];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int st = 128; st > 0; st >>= 1) {
+            if (threadIdx.x < st) sh[threadIdx.x] += sh[threadIdx.x + st];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = sh[0];
+        __syncthreads();
+    }
+}
+
+// Adjoint of the equilibrium initialisation g_j = f_eq,j(rho, u) - w_j rho_ref:
+// dL/drho = sum_j a_j w_j (1 + 3 cu + 9/2 cu^2 - 3/2 |u|^2),
+// dL/du   = sum_j a_j w_j rho (3 c + 9 cu c - 3 u) / lambda, with u in units of lambda.
+__global__ void k_equilibrium_vjp(const float* __restrict__ rho, const float* __restrict__ u,
+                                  const float* __restrict__ a, float* __restrict__ drho,
+                                  float* __restrict__ du, int64_t n, float inv_lambda) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float r = rho ? rho[i] : 1.0f;
+        const float ux = u[i] * inv_lambda, uy = u[n + i] * inv_lambda;
+        const float uu = ux * ux + uy * uy;
+        float gr = 0.f, gx = 0.f, gy = 0.f;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const float cx = (float)((j == 1 || j == 5 || j == 8) - (j == 3 || j == 6 || j == 7));
+            const float cy = (float)((j == 2 || j == 5 || j == 6) - (j == 4 || j == 7 || j == 8));
+            const float cu = cx * ux + cy * uy;
+            const float wa = wgt(j) * a[j * n + i];
+            gr += wa * (1.0f + 3.0f * cu + 4.5f * cu * cu - 1.5f * uu);
+            gx += wa * r * (3.0f * cx + 9.0f * cu * cx - 3.0f * ux);
+            gy += wa * r * (3.0f * cy + 9.0f * cu * cy - 3.0f * uy);
+        }
+        if (drho) drho[i] = gr;
+        if (du) {
+            du[i] = gx * inv_lambda;
+            du[n + i] = gy * inv_lambda;
+        }
+    }
+}
+
+// Adjoint of the moments (rho, u = lambda j / rho) of a stored state:
+// dL/dg_j = dL/drho + (lambda / rho) (dL/du . (c_j - j / rho)).
+__global__ void k_moments_vjp(const float* __restrict__ g, const float* __restrict__ drho,
+                              const float* __restrict__ du, float* __restrict__ out, int64_t n,
+                              float rho_ref, float lambda) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float h[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) h[j] = g[j * n + i];
+        const NodeMoments m = node_moments(h);
+        const float ir = 1.0f / (rho_ref + m.drho);
+        const float ux = m.jx * ir, uy = m.jy * ir;
+        const float br = drho ? drho[i] : 0.0f;
+        const float bx = du ? du[i] * lambda * ir : 0.0f;
+        const float by = du ? du[n + i] * lambda * ir : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const float cx = (float)((j == 1 || j == 5 || j == 8) - (j == 3 || j == 6 || j == 7));
+            const float cy = (float)((j == 2 || j == 5 || j == 6) - (j == 4 || j == 7 || j == 8));
+            out[j * n + i] = br + bx * (cx - ux) + by * (cy - uy);
+        }
+    }
+}
+
+// Kinetic energy L = 1/2 sum lambda^2 |j|^2 / rho (per-block FP64 partials in part[b*4]),
+// and optionally dL/dg_j = lambda^2 (c_j . j / rho - 1/2 |j|^2 / rho^2).
+__global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const float* __restrict__ g,
+                                                                   float* __restrict__ grad,
+                                                                   int64_t n, float rho_ref,
+                                                                   float lambda,
+                                                                   double* __restrict__ part) {
+    float ke = 0.0f;
+    const float l2 = lambda * lambda;
+    double acc = 0.0;
+    int cnt = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float h[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) h[j] = g[j * n + i];
+        const NodeMoments m = node_moments(h);
+        const float ir = 1.0f / (rho_ref + m.drho);
+        const float jj = m.jx * m.jx + m.jy * m.jy;
+        ke += 0.5f * l2 * jj * ir;
+        if (++cnt == 64) {  // keep the FP32 run short, accumulate in FP64
+            acc += (double)ke;
+            ke = 0.0f;
+            cnt = 0;
+        }
+        if (grad) {
+#pragma unroll
+            for (int j = 0; j < 9; ++j) {
+                const float cx = (float)((j == 1 || j == 5 || j == 8) - (j == 3 || j == 6 || j == 7));
+                const float cy = (float)((j == 2 || j == 5 || j == 6) - (j == 4 || j == 7 || j == 8));
+                grad[j * n + i] = l2 * ((cx * m.jx + cy * m.jy) * ir - 0.5f * jj * ir * ir);
+            }
+        }
+    }
+    acc += (double)ke;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFullMask, acc, o);
+    __shared__ double sh[kReduceThreads / 32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kReduceThreads / 32; ++w) s += sh[w];
+        part[4 * (int64_t)blockIdx.x] = s;
+    }
+}
+
+__global__ void k_partials_final(const double* __restrict__ part, int nblk,
+                                 double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += part[4 * b];
+        out[0] = s;
+    }
+}
+
+int grid1d(int64_t n, int threads) {
+    int64_t b = (n + threads - 1) / threads;
+    const int64_t cap = 152LL * 16;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
+
+template <int NV, int UM>
+cudaError_t adjoint_nv_um(const float* s_prev, const float* a_in, bool gather, float* mu_out,
+                          const AdjointArgs& aa, cudaStream_t st) {
+    const dim3 grid = adjoint_grid(aa.step.nx, aa.step.ny, NV);
+    if (gather)
+        k_adjoint_step<NV, UM, true><<<grid, kAdjThreads, 0, st>>>(s_prev, a_in, mu_out, aa);
+    else
+        k_adjoint_step<NV, UM, false><<<grid, kAdjThreads, 0, st>>>(s_prev, a_in, mu_out, aa);
+    return cudaGetLastError();
+}
+
+template <int NV>
+cudaError_t adjoint_nv(int um, const float* s_prev, const float* a_in, bool gather,
+                       float* mu_out, const AdjointArgs& aa, cudaStream_t st) {
+    switch (um) {
+        case UM_ZERO: return adjoint_nv_um<NV, UM_ZERO>(s_prev, a_in, gather, mu_out, aa, st);
+        case UM_FLUID: return adjoint_nv_um<NV, UM_FLUID>(s_prev, a_in, gather, mu_out, aa, st);
+        case UM_ANALYTIC:
+            return adjoint_nv_um<NV, UM_ANALYTIC>(s_prev, a_in, gather, mu_out, aa, st);
+        case UM_FIELD: return adjoint_nv_um<NV, UM_FIELD>(s_prev, a_in, gather, mu_out, aa, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+int adjoint_width(int nx) { return (nx % 4 == 0) ? 4 : 1; }
+
+dim3 adjoint_grid(int nx, int ny, int nv) {
+    const int threads_x = (nx / nv + (nx % nv ? 1 : 0));
+    return dim3((threads_x + kAdjThreads - 1) / kAdjThreads, ny < 65535 ? ny : 65535);
+}
+
+int64_t adjoint_blocks(int nx, int ny) {
+    const dim3 g = adjoint_grid(nx, ny, adjoint_width(nx));
+    return (int64_t)g.x * g.y;
+}
+
+cudaError_t launch_adjoint_step(int um, const float* s_prev, const float* a_in, bool gather,
+                                float* mu_out, const AdjointArgs& aa, cudaStream_t st) {
+    if (adjoint_width(aa.step.nx) == 4) return adjoint_nv<4>(um, s_prev, a_in, gather, mu_out, aa, st);
+    return adjoint_nv<1>(um, s_prev, a_in, gather, mu_out, aa, st);
+}
+
+cudaError_t launch_gather(const float* src, float* dst, int nx, int ny, cudaStream_t st) {
+    const int nv = adjoint_width(nx);
+    const dim3 grid = adjoint_grid(nx, ny, nv);
+    if (nv == 4)
+        k_gather<4><<<grid, kAdjThreads, 0, st>>>(src, dst, nx, ny);
+    else
+        k_gather<1><<<grid, kAdjThreads, 0, st>>>(src, dst, nx, ny);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acc_final(const double* acc, int64_t nblk, double* out, cudaStream_t st) {
+    k_acc_final<<<1, 256, 0, st>>>(acc, nblk, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_equilibrium_vjp(const float* rho, const float* u, const float* a, float* drho,
+                                   float* du, int64_t n, float inv_lambda, cudaStream_t st) {
+    k_equilibrium_vjp<<<grid1d(n, 256), 256, 0, st>>>(rho, u, a, drho, du, n, inv_lambda);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_vjp(const float* g, const float* drho, const float* du, float* out,
+                               int64_t n, float rho_ref, float lambda, cudaStream_t st) {
+    k_moments_vjp<<<grid1d(n, 256), 256, 0, st>>>(g, drho, du, out, n, rho_ref, lambda);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, float rho_ref,
+                                  float lambda, double* partials, int nblk, double* out,
+                                  cudaStream_t st) {
+    k_kinetic_energy<<<nblk, kReduceThreads, 0, st>>>(g, grad, n, rho_ref, lambda, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_partials_final<<<1, 32, 0, st>>>(partials, nblk, out);
+    return cudaGetLastError();
+}
+
+}  // namespace lbmrv

@@ -4,12 +4,11 @@
 
 #include "d2q9.cuh"
 #include "launch.h"
+#include "pull.cuh"
 
 namespace lbmrv {
 
 namespace {
-
-constexpr unsigned FULL = 0xffffffffu;
 
 // --------------------------------------------------------------------------------------
 // Fused step, one node per thread. Works for every lattice size (ragged rows, nx or
@@ -48,98 +47,44 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 
 // --------------------------------------------------------------------------------------
 // Fused step, NV consecutive nodes of a row per thread with aligned vector loads and
-// stores (requires nx % NV == 0 and 16-byte aligned planes). Populations moving along
-// +x / -x need the element one before / after the thread's aligned pack: it comes from
-// the neighbouring lane by a warp shuffle, and the lanes at a warp or row edge load it
-// directly (with the periodic wrap).
-template <typename T, int NV>
-struct alignas(sizeof(T) * NV) Pack {
-    T v[NV];
-};
-
-template <typename T, int NV>
-__device__ __forceinline__ void load_pack(const T* __restrict__ p, bool act, float out[NV]) {
-    if (act) {
-        const Pack<T, NV> pk = *reinterpret_cast<const Pack<T, NV>*>(p);
-#pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = to_f(pk.v[k]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) out[k] = 0.0f;
-    }
-}
-
-// Row segment pulled from x - 1: (prev, v0, ..., v_{NV-2}).
-template <typename T, int NV>
-__device__ __forceinline__ void load_from_left(const T* __restrict__ row, int x0, int xprev,
-                                               bool act, bool edge, float out[NV]) {
-    float v[NV];
-    load_pack<T, NV>(row + x0, act, v);
-    float prev = __shfl_up_sync(FULL, v[NV - 1], 1);
-    if (edge && act) prev = to_f(row[xprev]);
-    out[0] = prev;
-#pragma unroll
-    for (int k = 1; k < NV; ++k) out[k] = v[k - 1];
-}
-
-// Row segment pulled from x + 1: (v1, ..., v_{NV-1}, next).
-template <typename T, int NV>
-__device__ __forceinline__ void load_from_right(const T* __restrict__ row, int x0, int xnext,
-                                                bool act, bool edge, float out[NV]) {
-    float v[NV];
-    load_pack<T, NV>(row + x0, act, v);
-    float next = __shfl_down_sync(FULL, v[0], 1);
-    if (edge && act) next = to_f(row[xnext]);
-#pragma unroll
-    for (int k = 0; k < NV - 1; ++k) out[k] = v[k + 1];
-    out[NV - 1] = next;
-}
-
+// stores (requires nx % NV == 0 and 16-byte aligned planes); row loads in pull.cuh.
 template <typename T, int NV, int UM>
 __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                                                   T* __restrict__ dst, StepArgs a) {
     const int nx = a.nx, ny = a.ny;
     const int64_t n = (int64_t)nx * ny;
-    const int lane = threadIdx.x & 31;
-    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * NV;
-    const bool act = x0 < nx;
-    const bool left_edge = lane == 0;  // lane - 1 exists and is active otherwise
-    const bool right_edge = lane == 31 || x0 + NV >= nx;
-    const int xprev = x0 == 0 ? nx - 1 : x0 - 1;
-    const int xnext = x0 + NV >= nx ? 0 : x0 + NV;
+    const PackLane p = pack_lane<NV>(nx);
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
         const int ym = y == 0 ? ny - 1 : y - 1;
         const int yp = y == ny - 1 ? 0 : y + 1;
         const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
         float g[9][NV];
-        load_pack<T, NV>(src + r0 + x0, act, g[0]);
-        load_from_left<T, NV>(src + n + r0, x0, xprev, act, left_edge, g[1]);
-        load_pack<T, NV>(src + 2 * n + rm + x0, act, g[2]);
-        load_from_right<T, NV>(src + 3 * n + r0, x0, xnext, act, right_edge, g[3]);
-        load_pack<T, NV>(src + 4 * n + rp + x0, act, g[4]);
-        load_from_left<T, NV>(src + 5 * n + rm, x0, xprev, act, left_edge, g[5]);
-        load_from_right<T, NV>(src + 6 * n + rm, x0, xnext, act, right_edge, g[6]);
-        load_from_right<T, NV>(src + 7 * n + rp, x0, xnext, act, right_edge, g[7]);
-        load_from_left<T, NV>(src + 8 * n + rp, x0, xprev, act, left_edge, g[8]);
-        if (act) {
+        pull_pack<T, NV>(src, n, r0, rm, rp, p, g);
+        if (p.act) {
+            // analytic prescribed field: one sincospi per thread, then angle addition
+            float ux_row = 0.0f, s0 = 0.0f, c0 = 0.0f;
+            if (UM == UM_ANALYTIC) {
+                ux_row = a.amp_t * cospif(a.two_over_ny * (float)y);
+                sincospif(a.two_over_nx * (float)p.x0, &s0, &c0);
+            }
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
                 float h[9];
 #pragma unroll
                 for (int j = 0; j < 9; ++j) h[j] = g[j][k];
                 float ux, uy;
-                relative_velocity<UM>(h, a.rho_ref, x0 + k, y, r0 + x0 + k, a, ux, uy);
+                if (UM == UM_ANALYTIC) {
+                    ux = ux_row;
+                    uy = a.amp_t * (s0 * a.cos_k[k] + c0 * a.sin_k[k]);
+                } else {
+                    relative_velocity<UM>(h, a.rho_ref, p.x0 + k, y, r0 + p.x0 + k, a, ux, uy);
+                }
                 relax_node(h, ux, uy, a.s, a.rho_ref);
 #pragma unroll
                 for (int j = 0; j < 9; ++j) g[j][k] = h[j];
             }
 #pragma unroll
-            for (int j = 0; j < 9; ++j) {
-                Pack<T, NV> pk;
-#pragma unroll
-                for (int k = 0; k < NV; ++k) pk.v[k] = from_f<T>(g[j][k]);
-                *reinterpret_cast<Pack<T, NV>*>(dst + j * n + r0 + x0) = pk;
-            }
+            for (int j = 0; j < 9; ++j) store_pack<T, NV>(dst + j * n + r0 + p.x0, g[j]);
         }
     }
 }
@@ -196,7 +141,7 @@ __global__ void k_moments(const T* __restrict__ src, float* __restrict__ rho,
 // order, so the result is deterministic.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
     return v;
 }
 
@@ -224,18 +169,33 @@ template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* __restrict__ src,
                                                                       int64_t n,
                                                                       double* __restrict__ part) {
+    // Node moments are FP32; each thread adds runs of up to 32 of them in FP32 and the
+    // runs in FP64 (FP64 adds are scarce on this GPU; a run of 32 loses < 1e-6 relative).
     double v[4] = {0.0, 0.0, 0.0, 0.0};
+    float r[3] = {0.f, 0.f, 0.f};
+    int run = 0, bad = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float g[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * n + i]);
         const NodeMoments m = node_moments(g);
-        v[0] += (double)m.drho;
-        v[1] += (double)m.jx;
-        v[2] += (double)m.jy;
-        v[3] += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy)) ? 0.0 : 1.0;
+        r[0] += m.drho;
+        r[1] += m.jx;
+        r[2] += m.jy;
+        bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy)) ? 0 : 1;
+        if (++run == 32) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] += (double)r[c];
+                r[c] = 0.f;
+            }
+            run = 0;
+        }
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] += (double)r[c];
+    v[3] = (double)bad;
     block_sum4<kReduceThreads>(v, part + 4 * (int64_t)blockIdx.x);
 }
 
@@ -308,8 +268,10 @@ cudaError_t step_dispatch_um(const void* src, void* dst, const StepArgs& a, cuda
 }  // namespace
 
 int step_vector_width(int storage, int nx) {
-    // Widest pack that divides nx: 16-byte packs for FP32 (4) and 2-byte types (8).
-    const int widest = storage == kStoreF32 ? 4 : 8;
+    // Widest pack of at most 4 nodes that divides nx: 16-byte packs for FP32, 8-byte packs
+    // for the 16-bit types (8-node packs need ~120 registers and ran slower on GB300).
+    const int widest = 4;
+    (void)storage;
     for (int nv = widest; nv > 1; nv >>= 1)
         if (nx % nv == 0 && nx >= nv) return nv;
     return 1;

@@ -34,4 +34,30 @@ cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho
                              double lambda, double* partials, int nblk, double* out,
                              cudaStream_t st);
 
+// ---------------------------------------------------------------- adjoint (FP32 state)
+struct AdjointArgs {
+    StepArgs step;     // step arguments of the relaxation being reversed (time k)
+    float da_factor;   // d(u~/lambda)/dA = cos(2 pi k / P) / lambda for dL/dA
+    float* dut0;       // optional [2][n]: accumulates amp_t * dL/d(u~/lambda) per node
+    double* acc;       // per-block FP64 accumulators, 8 per block (6 rates, dL/dA, unused)
+};
+
+int adjoint_width(int nx);
+dim3 adjoint_grid(int nx, int ny, int nv);
+int64_t adjoint_blocks(int nx, int ny);
+
+// mu_out = J_C(P s_prev)^T a, a = (gather ? P^T a_in : a_in); accumulates into aa.acc.
+cudaError_t launch_adjoint_step(int um, const float* s_prev, const float* a_in, bool gather,
+                                float* mu_out, const AdjointArgs& aa, cudaStream_t st);
+cudaError_t launch_gather(const float* src, float* dst, int nx, int ny, cudaStream_t st);
+cudaError_t launch_acc_final(const double* acc, int64_t nblk, double* out, cudaStream_t st);
+cudaError_t launch_equilibrium_vjp(const float* rho, const float* u, const float* a, float* drho,
+                                   float* du, int64_t n, float inv_lambda, cudaStream_t st);
+cudaError_t launch_moments_vjp(const float* g, const float* drho, const float* du, float* out,
+                               int64_t n, float rho_ref, float lambda, cudaStream_t st);
+// partials: 4 * nblk doubles of scratch (slot 0 of each used); out: 1 double (device).
+cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, float rho_ref,
+                                  float lambda, double* partials, int nblk, double* out,
+                                  cudaStream_t st);
+
 }  // namespace lbmrv

@@ -1,0 +1,204 @@
+// C ABI of the discrete adjoint: checkpointed forward, reverse sweep, and the adjoints
+// of the equilibrium initialisation, of the moments and of the kinetic energy.
+#include <cuda_runtime.h>
+
+#include "handle.h"
+#include "launch.h"
+#include "lbmrv.h"
+
+using namespace lbmrv;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Workspace: C checkpoints S_{t0 + c seg} (c = 0 .. C-1), seg - 1 recomputed states of the
+// current segment, two adjoint states, then 8 FP64 accumulators per adjoint block and 8
+// results.
+struct WsLayout {
+    int64_t C = 0, seg = 0, nblk = 0;
+    size_t state = 0, off_seg = 0, off_mu = 0, off_acc = 0, total = 0;
+};
+
+WsLayout layout(const lbmrv_s* h, int64_t n, int64_t seg) {
+    WsLayout L;
+    L.seg = seg;
+    L.C = (n + seg - 1) / seg;
+    L.state = round_up((size_t)(9 * h->n) * sizeof(float));
+    L.nblk = adjoint_blocks((int)h->nx, (int)h->ny);
+    L.off_seg = (size_t)L.C * L.state;
+    L.off_mu = L.off_seg + (size_t)(seg - 1) * L.state;
+    L.off_acc = L.off_mu + 2 * L.state;
+    L.total = L.off_acc + round_up((size_t)(L.nblk + 1) * 8 * sizeof(double));
+    return L;
+}
+
+int check_common(lbmrv_t h, int64_t n, int64_t seg, const void* ws, size_t ws_bytes,
+                 const char* who, WsLayout* out) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "%s: NULL handle", who);
+    if (h->storage != LBMRV_FP32)
+        return fail(h, LBMRV_E_UNSUPPORTED, "%s: the adjoint needs FP32 storage", who);
+    if (n < 1 || seg < 1 || seg > n)
+        return fail(h, LBMRV_E_INVAL, "%s: need n >= 1 and 1 <= seg <= n", who);
+    if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign)
+        return fail(h, LBMRV_E_INVAL, "%s: workspace must be a 256-byte aligned device buffer",
+                    who);
+    *out = layout(h, n, seg);
+    if (ws_bytes < out->total)
+        return fail(h, LBMRV_E_NOMEM, "%s: workspace of %zu bytes, %zu needed", who, ws_bytes,
+                    out->total);
+    return LBMRV_OK;
+}
+
+char* at(void* ws, size_t off) { return static_cast<char*>(ws) + off; }
+
+}  // namespace
+
+extern "C" {
+
+int64_t lbmrv_adjoint_workspace_bytes(lbmrv_t h, int64_t n, int64_t seg) {
+    if (!h || n < 1 || seg < 1 || seg > n) return -1;
+    return (int64_t)layout(h, n, seg).total;
+}
+
+int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
+                               size_t ws_bytes) {
+    WsLayout L;
+    int rc = check_common(h, n, seg, ws_dev, ws_bytes, "lbmrv_forward_checkpointed", &L);
+    if (rc != LBMRV_OK) return rc;
+    DeviceGuard g(h->device);
+    const size_t bytes = (size_t)(9 * h->n) * sizeof(float);
+    const int um = kernel_mode(h);
+    const int nv = choose_width(h, h->f[0], h->f[1]);
+    const int64_t t0 = h->t;
+    cudaError_t e = cudaMemcpyAsync(at(ws_dev, 0), h->f[h->cur], bytes, cudaMemcpyDeviceToDevice,
+                                    h->stream);
+    for (int64_t k = 1; k <= n && e == cudaSuccess; ++k) {
+        e = launch_step(h->storage, um, nv, h->f[h->cur], h->f[1 - h->cur], make_args(h, t0 + k),
+                        h->stream);
+        h->cur = 1 - h->cur;
+        h->t = t0 + k;
+        if (e == cudaSuccess && k % seg == 0 && k < n)
+            e = cudaMemcpyAsync(at(ws_dev, (size_t)(k / seg) * L.state), h->f[h->cur], bytes,
+                                cudaMemcpyDeviceToDevice, h->stream);
+    }
+    if (e != cudaSuccess) {
+        h->ckpt_valid = false;
+        return cuda_fail(h, e, "lbmrv_forward_checkpointed");
+    }
+    h->ckpt_valid = true;
+    h->ckpt_n = n;
+    h->ckpt_seg = seg;
+    h->ckpt_t0 = t0;
+    h->ckpt_ws = ws_dev;
+    return LBMRV_OK;
+}
+
+int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_bytes,
+                  const float* dL_dS_dev, float* dL_dS0_dev, double* dL_ds_host,
+                  double* dL_damp_host, float* dL_dut0_dev) {
+    WsLayout L;
+    int rc = check_common(h, n, seg, ws_dev, ws_bytes, "lbmrv_adjoint", &L);
+    if (rc != LBMRV_OK) return rc;
+    if (!dL_dS_dev || !dL_dS0_dev)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_adjoint: dL/dS_N and dL/dS_0 buffers are required");
+    if (!h->ckpt_valid || h->ckpt_n != n || h->ckpt_seg != seg || h->ckpt_ws != ws_dev)
+        return fail(h, LBMRV_E_INVAL,
+                    "lbmrv_adjoint: no matching lbmrv_forward_checkpointed(n, seg, ws) before");
+    DeviceGuard g(h->device);
+    const int64_t t0 = h->ckpt_t0;
+    const int um = kernel_mode(h);
+    const int nv = choose_width(h, ws_dev, ws_dev);
+    double* acc = reinterpret_cast<double*>(at(ws_dev, L.off_acc));
+    double* res = acc + 8 * L.nblk;
+    float* mu[2] = {reinterpret_cast<float*>(at(ws_dev, L.off_mu)),
+                    reinterpret_cast<float*>(at(ws_dev, L.off_mu + L.state))};
+    cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)L.nblk * 8 * sizeof(double), h->stream);
+    if (e == cudaSuccess && dL_dut0_dev)
+        e = cudaMemsetAsync(dL_dut0_dev, 0, (size_t)(2 * h->n) * sizeof(float), h->stream);
+    const float* a = dL_dS_dev;
+    bool gather = false;
+    int pp = 0;
+    for (int64_t c = L.C - 1; c >= 0 && e == cudaSuccess; --c) {
+        const int64_t base = c * seg;
+        const int64_t khi = base + seg < n ? base + seg : n;
+        const float* ck = reinterpret_cast<const float*>(at(ws_dev, (size_t)c * L.state));
+        auto seg_state = [&](int64_t k) {  // S_k for base < k < khi
+            return reinterpret_cast<float*>(at(ws_dev, L.off_seg + (size_t)(k - base - 1) * L.state));
+        };
+        const float* src = ck;
+        for (int64_t k = base + 1; k < khi && e == cudaSuccess; ++k) {
+            e = launch_step(LBMRV_FP32, um, nv, src, seg_state(k), make_args(h, t0 + k), h->stream);
+            src = seg_state(k);
+        }
+        for (int64_t k = khi; k > base && e == cudaSuccess; --k) {
+            const float* s_prev = (k - 1 == base) ? ck : seg_state(k - 1);
+            AdjointArgs aa;
+            aa.step = make_args(h, t0 + k);
+            aa.da_factor = (float)(time_factor(h, t0 + k) / h->lambda);
+            aa.dut0 = dL_dut0_dev;
+            aa.acc = acc;
+            e = launch_adjoint_step(um, s_prev, a, gather, mu[pp], aa, h->stream);
+            a = mu[pp];
+            gather = true;
+            pp ^= 1;
+        }
+    }
+    if (e == cudaSuccess) e = launch_gather(a, dL_dS0_dev, (int)h->nx, (int)h->ny, h->stream);
+    if (e == cudaSuccess) e = launch_acc_final(acc, L.nblk, res, h->stream);
+    double out[8] = {0};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_adjoint");
+    if (dL_ds_host) {
+        dL_ds_host[0] = dL_ds_host[1] = dL_ds_host[2] = 0.0;
+        for (int k = 0; k < 6; ++k) dL_ds_host[3 + k] = out[k];
+    }
+    if (dL_damp_host) *dL_damp_host = out[6];
+    return LBMRV_OK;
+}
+
+int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
+    if (!h || !ke_host) return fail(h, LBMRV_E_INVAL, "lbmrv_kinetic_energy: NULL argument");
+    if (h->storage != LBMRV_FP32)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_kinetic_energy: needs FP32 storage");
+    DeviceGuard g(h->device);
+    double* res = h->red + 4 * (size_t)h->red_blocks;
+    cudaError_t e = launch_kinetic_energy(static_cast<const float*>(h->f[h->cur]), dL_dS_dev, h->n,
+                                          (float)h->rho_ref, (float)h->lambda, h->red,
+                                          h->red_blocks, res, h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ke_host, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_kinetic_energy");
+    return LBMRV_OK;
+}
+
+int lbmrv_moments_vjp(lbmrv_t h, const float* dL_drho_dev, const float* dL_du_dev,
+                      float* dL_dS_dev) {
+    if (!h || !dL_dS_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_moments_vjp: NULL argument");
+    if (h->storage != LBMRV_FP32)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_moments_vjp: needs FP32 storage");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_moments_vjp(static_cast<const float*>(h->f[h->cur]), dL_drho_dev,
+                                       dL_du_dev, dL_dS_dev, h->n, (float)h->rho_ref,
+                                       (float)h->lambda, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_moments_vjp");
+    return LBMRV_OK;
+}
+
+int lbmrv_equilibrium_vjp(lbmrv_t h, const float* rho_dev, const float* u_dev,
+                          const float* dL_dS0_dev, float* dL_drho_dev, float* dL_du_dev) {
+    if (!h || !u_dev || !dL_dS0_dev)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_equilibrium_vjp: NULL argument");
+    DeviceGuard g(h->device);
+    cudaError_t e = launch_equilibrium_vjp(rho_dev, u_dev, dL_dS0_dev, dL_drho_dev, dL_du_dev, h->n,
+                                           (float)(1.0 / h->lambda), h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_equilibrium_vjp");
+    return LBMRV_OK;
+}
+
+}  // extern "C"

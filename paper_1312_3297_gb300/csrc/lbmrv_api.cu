@@ -7,35 +7,17 @@
 #include <cstring>
 #include <new>
 
-#include "lbmrv.h"
+#include "handle.h"
 #include "launch.h"
+#include "lbmrv.h"
 
 using namespace lbmrv;
 
-struct lbmrv_s {
-    int lattice = LBMRV_D2Q9;
-    int umode = LBMRV_UT_ZERO;
-    int storage = LBMRV_FP32;
-    int device = 0;
-    int width = 0;  // 0: automatic kernel choice; else nodes per thread of the fused step
-    int64_t nx = 0, ny = 0, n = 0;
-    double lambda = 1.0, rho_ref = 0.0;
-    double s[9] = {0};
-    cudaStream_t stream = nullptr;
-    void* f[2] = {nullptr, nullptr};
-    bool owns_f = false;
-    int cur = 0;
-    int64_t t = 0;
-    const float* ut0 = nullptr;
-    double amp = 0.0, period = 0.0;
-    double* red = nullptr;  // reduction scratch: 4 * red_blocks partials + 4 results
-    int red_blocks = 0;
-    char err[320] = {0};
-};
+namespace lbmrv {
 
 namespace {
-
 thread_local char g_create_err[320] = {0};
+}  // namespace
 
 int fail(lbmrv_t h, int code, const char* fmt, ...) {
     char* buf = h ? h->err : g_create_err;
@@ -46,69 +28,19 @@ int fail(lbmrv_t h, int code, const char* fmt, ...) {
     return code;
 }
 
-int cuda_fail(lbmrv_t h, cudaError_t e, const char* what) {
-    return fail(h, LBMRV_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-int64_t elem_size(int storage) {
-    switch (storage) {
-        case LBMRV_FP32: return 4;
-        case LBMRV_FP16:
-        case LBMRV_BF16: return 2;
-        default: return -1;
-    }
-}
-
-// Make the handle's device current for the duration of a call.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = true;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) != cudaSuccess) {
-            ok = false;
-            return;
-        }
-        if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-    }
-    ~DeviceGuard() {
-        int now = -1;
-        if (prev >= 0 && cudaGetDevice(&now) == cudaSuccess && now != prev) cudaSetDevice(prev);
-    }
-};
-
-StepArgs make_args(const lbmrv_s* h, int64_t t) {
-    StepArgs a;
-    a.nx = (int)h->nx;
-    a.ny = (int)h->ny;
-    a.s = Rates{(float)h->s[3], (float)h->s[4], (float)h->s[5],
-                (float)h->s[6], (float)h->s[7], (float)h->s[8]};
-    a.rho_ref = (float)h->rho_ref;
-    double tf = 1.0;
-    if (h->period > 0.0) tf = std::cos(2.0 * M_PI * (double)t / h->period);
-    a.amp_t = (float)(h->amp * tf / h->lambda);
-    a.two_over_nx = (float)(2.0 / (double)h->nx);
-    a.two_over_ny = (float)(2.0 / (double)h->ny);
-    a.ut0 = h->ut0;
-    return a;
-}
-
-int kernel_mode(const lbmrv_s* h) {
-    if (h->umode == LBMRV_UT_ZERO) return UM_ZERO;
-    if (h->umode == LBMRV_UT_FLUID) return UM_FLUID;
-    return h->ut0 ? UM_FIELD : UM_ANALYTIC;
-}
-
-int choose_width(const lbmrv_s* h) {
+int choose_width(const lbmrv_s* h, const void* a, const void* b) {
     if (h->width > 0) return h->width;
     const int nv = step_vector_width(h->storage, (int)h->nx);
     const size_t align = (size_t)(nv * elem_size(h->storage));
-    if (nv > 1 && ((reinterpret_cast<uintptr_t>(h->f[0]) % align) != 0 ||
-                   (reinterpret_cast<uintptr_t>(h->f[1]) % align) != 0))
+    if (nv > 1 && ((reinterpret_cast<uintptr_t>(a) % align) != 0 ||
+                   (reinterpret_cast<uintptr_t>(b) % align) != 0))
         return 1;
     return nv;
 }
 
-}  // namespace
+const char* last_create_error() { return g_create_err; }
+
+}  // namespace lbmrv
 
 extern "C" {
 
@@ -216,7 +148,7 @@ int lbmrv_destroy(lbmrv_t h) {
     return LBMRV_OK;
 }
 
-const char* lbmrv_last_error(lbmrv_t h) { return h ? h->err : g_create_err; }
+const char* lbmrv_last_error(lbmrv_t h) { return h ? h->err : last_create_error(); }
 
 int lbmrv_set_stream(lbmrv_t h, void* stream) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_stream: NULL handle");
@@ -240,6 +172,19 @@ int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread) {
     if (reinterpret_cast<uintptr_t>(h->f[0]) % align || reinterpret_cast<uintptr_t>(h->f[1]) % align)
         return fail(h, LBMRV_E_INVAL, "lbmrv_set_kernel_width: buffers not aligned for %d", w);
     h->width = w;
+    return LBMRV_OK;
+}
+
+int lbmrv_set_rates(lbmrv_t h, const double* s) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_rates: NULL handle");
+    if (!s) return fail(h, LBMRV_E_INVAL, "lbmrv_set_rates: s is NULL");
+    for (int k = 0; k < 3; ++k)
+        if (s[k] != 0.0)
+            return fail(h, LBMRV_E_INVAL, "lbmrv_set_rates: s[%d] must be 0 (conserved moment)", k);
+    for (int k = 3; k < 9; ++k)
+        if (!std::isfinite(s[k]))
+            return fail(h, LBMRV_E_INVAL, "lbmrv_set_rates: s[%d] is not finite", k);
+    for (int k = 0; k < 9; ++k) h->s[k] = s[k];
     return LBMRV_OK;
 }
 
@@ -288,7 +233,7 @@ int lbmrv_step(lbmrv_t h, int64_t n) {
     if (n < 0) return fail(h, LBMRV_E_INVAL, "lbmrv_step: n < 0");
     DeviceGuard g(h->device);
     const int um = kernel_mode(h);
-    const int nv = choose_width(h);
+    const int nv = choose_width(h, h->f[0], h->f[1]);
     for (int64_t k = 0; k < n; ++k) {
         const StepArgs a = make_args(h, h->t + 1);
         cudaError_t e = launch_step(h->storage, um, nv, h->f[h->cur], h->f[1 - h->cur], a,

@@ -52,6 +52,8 @@ class D2Q9:
                                     self.mode, self.storage, self.rho_ref, self.stream,
                                     self._bufs[0], self._bufs[1])
         self._ut0 = None
+        self.s = [float(v) for v in s]
+        self.amp, self.period = 0.0, 0.0
         self.dtype = STORAGE_DTYPES[self.storage]
 
     # -- lifecycle
@@ -76,7 +78,12 @@ class D2Q9:
     def set_kernel_width(self, nodes_per_thread: int):
         B.lbmrv_set_kernel_width(self.h, nodes_per_thread)
 
+    def set_rates(self, s):
+        B.lbmrv_set_rates(self.h, list(s))
+        self.s = [float(v) for v in s]
+
     def set_utilde(self, ut0=None, amplitude: float = 0.0, period: float = 0.0):
+        self.amp, self.period = float(amplitude), float(period)
         if ut0 is not None:
             ut0 = torch.as_tensor(ut0, dtype=torch.float32, device=self.device).contiguous()
             if ut0.numel() != 2 * self.n:
@@ -136,3 +143,47 @@ class D2Q9:
 
     def state_ptr(self) -> int:
         return B.lbmrv_state_ptr(self.h)
+
+    # -- adjoint (FP32 storage)
+    def adjoint_workspace(self, n: int, seg: int) -> torch.Tensor:
+        nbytes = B.lbmrv_adjoint_workspace_bytes(self.h, n, seg)
+        if nbytes <= 0:
+            raise ValueError(f"invalid adjoint window n={n}, seg={seg}")
+        return torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def forward_checkpointed(self, n: int, seg: int, ws: torch.Tensor):
+        B.lbmrv_forward_checkpointed(self.h, n, seg, ws, ws.numel())
+
+    def adjoint(self, n: int, seg: int, ws: torch.Tensor, dL_dS: torch.Tensor,
+                field_grad: bool = False):
+        """Reverse sweep of the last forward_checkpointed(n, seg, ws). Returns
+        (dL/dS_0 [9, ny, nx], dL/ds [9], dL/dA, dL/du~0 [2, ny, nx] or None)."""
+        d0 = torch.empty((9, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        dut = (torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
+               if field_grad else None)
+        ds, da = B.lbmrv_adjoint(self.h, n, seg, ws, ws.numel(), dL_dS.contiguous(), d0, dut)
+        return d0, ds, da, dut
+
+    def kinetic_energy(self, grad: bool = False):
+        g = (torch.empty((9, self.ny, self.nx), dtype=torch.float32, device=self.device)
+             if grad else None)
+        ke = B.lbmrv_kinetic_energy(self.h, g)
+        return ke, g
+
+    def moments_vjp(self, dL_drho=None, dL_du=None) -> torch.Tensor:
+        out = torch.empty((9, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        if dL_drho is not None:
+            dL_drho = dL_drho.to(torch.float32).contiguous()
+        if dL_du is not None:
+            dL_du = dL_du.to(torch.float32).contiguous()
+        B.lbmrv_moments_vjp(self.h, dL_drho, dL_du, out)
+        self._keep = (dL_drho, dL_du)
+        return out
+
+    def equilibrium_vjp(self, rho, u, dL_dS0):
+        """rho [ny, nx] or None, u [2, ny, nx] (device float32)."""
+        drho = torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device)
+        du = torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        B.lbmrv_equilibrium_vjp(self.h, None if rho is None else rho.contiguous(),
+                                u.contiguous(), dL_dS0.contiguous(), drho, du)
+        return drho, du

@@ -60,3 +60,42 @@ def rel_errors(f_g, m_g, f_o, m_o):
     e_u = du / max(np.hypot(ux_o, uy_o).max(), 1e-300)
     e_f = np.abs(f_g - f_o).max() / np.abs(f_o).max()
     return e_rho, e_u, e_f
+
+
+def oracle_kinetic_energy(rho0, u0, s, mode, steps, amp=0.0, period=0.0, ut0=None,
+                          method=1, nthreads=8):
+    """FP64 oracle: L = 1/2 sum |q|^2 / rho after `steps` steps from f_eq(rho0, u0)."""
+    import oracle
+
+    f0 = oracle.init_equilibrium(rho0, u0[0], u0[1], 1.0)
+    f = oracle.run(f0, 1.0, np.asarray(s, float), MODES[mode], steps, method=method,
+                   ut0=ut0, amp=amp, period=period, nthreads=nthreads)
+    r, ux, uy = oracle.moments(f, 1.0)
+    return 0.5 * float((r * (ux * ux + uy * uy)).sum())
+
+
+def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=None,
+                  field_grad=False):
+    """Kinetic energy after `steps` steps and its gradients from the CUDA adjoint:
+    (L, dL/du0 [2, ny, nx], dL/ds [9], dL/dA, dL/du~0 or None)."""
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9
+
+    rho, ux, uy = fields
+    sim = D2Q9(nx, ny, s, mode=mode)
+    if MODES[mode] == 2:
+        sim.set_utilde(None if ut0 is None else torch.as_tensor(ut0, dtype=torch.float32),
+                       amp, period)
+    rho_t = torch.as_tensor(rho, dtype=torch.float32, device="cuda")
+    u_t = torch.as_tensor(np.stack([ux, uy]), dtype=torch.float32, device="cuda")
+    sim.init_equilibrium(rho_t, u_t[0], u_t[1])
+    ws = sim.adjoint_workspace(steps, seg)
+    sim.forward_checkpointed(steps, seg, ws)
+    ke, dLdS = sim.kinetic_energy(grad=True)
+    d0, ds, da, dut = sim.adjoint(steps, seg, ws, dLdS, field_grad=field_grad)
+    _, du0 = sim.equilibrium_vjp(rho_t, u_t, d0)
+    out = (ke, du0.double().cpu().numpy(), ds, da,
+           None if dut is None else dut.double().cpu().numpy())
+    sim.close()
+    return out

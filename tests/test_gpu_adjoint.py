@@ -1,0 +1,167 @@
+"""GPU discrete adjoint against the FP64 references.
+
+The CUDA reverse sweep (lbmrv_forward_checkpointed + lbmrv_adjoint, through the C ABI)
+gives the gradient of the final kinetic energy L = 1/2 sum |q|^2/rho with respect to the
+initial velocity field, the shear rate s_nu and the amplitude A of a prescribed u~. It is
+compared with reverse-mode differentiation of the FP64 PyTorch statement of the scheme and
+with central differences (eps = 1e-4) of the FP64 C oracle; the bar is 1e-4 relative error.
+"""
+import numpy as np
+import pytest
+
+import lbm_inputs as inp
+from pairs import f32_fields, gpu_gradients, oracle_kinetic_energy
+
+pytestmark = pytest.mark.gpu
+
+S = [0, 0, 0, 1.4, 1.9, 1.9, 1.2, 1.2, 1.4]
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed"])
+def test_adjoint_matches_fp64_reverse_mode(mode):
+    from oracle import torch_ref as tr
+
+    nx, ny, steps, seg = 48, 40, 40, 7
+    fields = f32_fields(inp.noisy_shear_wave(nx, ny, seed=0))
+    rho, ux, uy = fields
+    u0 = np.stack([ux, uy])
+    amp, period = 0.03, 50.0
+    L, du0, ds, da, _ = gpu_gradients(nx, ny, S, mode, steps, seg, fields, amp, period)
+    mid = {"zero": 0, "fluid": 1, "prescribed": 2}[mode]
+    Lr, gur, gsr, gar = tr.loss_and_grads(rho, u0, 1.0, S, 1.9, mid, steps,
+                                          tr.analytic_base_field(nx, ny), amp, period)
+    assert abs(L - Lr) <= 1e-6 * abs(Lr)
+    assert _rel(du0, gur) <= TOL
+    assert abs(ds[4] + ds[5] - gsr) <= TOL * abs(gsr)
+    if mode == "prescribed":
+        assert abs(da - gar) <= TOL * abs(gar)
+    else:
+        assert da == 0.0
+
+
+def test_adjoint_64x64_shear_wave_against_reverse_mode():
+    """The 64^2 check of the adjoint workload: noisy shear wave u_x = 0.05 sin 2pi y/L +
+    N(0, 0.01), prescribed u~ with A = 0.03, P = 1000."""
+    from oracle import torch_ref as tr
+
+    n, steps, seg = 64, 64, 8
+    fields = f32_fields(inp.noisy_shear_wave(n, n, seed=0))
+    rho, ux, uy = fields
+    L, du0, ds, da, _ = gpu_gradients(n, n, S, "prescribed", steps, seg, fields, 0.03, 1000.0)
+    Lr, gur, gsr, gar = tr.loss_and_grads(rho, np.stack([ux, uy]), 1.0, S, 1.9, 2, steps,
+                                          tr.analytic_base_field(n, n), 0.03, 1000.0)
+    assert _rel(du0, gur) <= TOL
+    assert abs(ds[4] + ds[5] - gsr) <= TOL * abs(gsr)
+    assert abs(da - gar) <= TOL * abs(gar)
+
+
+def test_adjoint_matches_central_differences_of_the_oracle():
+    """Central differences (eps = 1e-4) of the FP64 oracle's kinetic energy, 128^2 x 200
+    steps, prescribed u~: s_nu, A, and two random directions of the initial velocity."""
+    n, steps, seg = 128, 200, 15
+    fields = f32_fields(inp.noisy_shear_wave(n, n, seed=1))
+    rho, ux, uy = fields
+    u0 = np.stack([ux, uy])
+    amp, period = 0.03, 150.0
+    base = inp.to_f32_exact(np.stack([
+        np.cos(2 * np.pi * np.arange(n)[:, None] / n) * np.ones((1, n)),
+        np.sin(2 * np.pi * np.arange(n)[None, :] / n) * np.ones((n, 1))]))
+    L, du0, ds, da, _ = gpu_gradients(n, n, S, "prescribed", steps, seg, fields, amp, period)
+    eps = 1e-4
+
+    def ke(s_nu=1.9, a=amp, u=u0):
+        s = list(S)
+        s[4] = s[5] = s_nu
+        return oracle_kinetic_energy(rho, u, s, "prescribed", steps, a, period, base)
+
+    fd_s = (ke(s_nu=1.9 + eps) - ke(s_nu=1.9 - eps)) / (2 * eps)
+    fd_a = (ke(a=amp + eps) - ke(a=amp - eps)) / (2 * eps)
+    assert abs(ds[4] + ds[5] - fd_s) <= TOL * abs(fd_s), (ds[4] + ds[5], fd_s)
+    assert abs(da - fd_a) <= TOL * abs(fd_a), (da, fd_a)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        v = rng.standard_normal(u0.shape)
+        v /= np.abs(v).max()
+        fd_v = (ke(u=u0 + eps * v) - ke(u=u0 - eps * v)) / (2 * eps)
+        g_v = float((du0 * v).sum())
+        assert abs(g_v - fd_v) <= TOL * abs(fd_v), (g_v, fd_v)
+
+
+def test_field_gradient_is_consistent_with_amplitude_gradient():
+    """L depends on A and u~0 only through A u~0(x), so A dL/dA = sum_x u~0 . dL/du~0."""
+    nx, ny, steps = 64, 48, 60
+    fields = f32_fields(inp.noisy_shear_wave(nx, ny, seed=3))
+    ut0 = inp.to_f32_exact(inp.prescribed_base_field(nx, ny, seed=2, smooth=False))
+    amp = 0.02
+    for field in (None, ut0):
+        L, du0, ds, da, dut = gpu_gradients(nx, ny, S, "prescribed", steps, 10, fields, amp,
+                                            40.0, ut0=field, field_grad=True)
+        base = field if field is not None else np.stack([
+            np.cos(2 * np.pi * np.arange(ny)[:, None] / ny) * np.ones((1, nx)),
+            np.sin(2 * np.pi * np.arange(nx)[None, :] / nx) * np.ones((ny, 1))])
+        np.testing.assert_allclose(amp * da, (base * dut).sum(), rtol=1e-4)
+
+
+def test_checkpoint_interval_does_not_change_the_gradient():
+    nx, ny, steps = 96, 64, 90
+    fields = f32_fields(inp.noisy_shear_wave(nx, ny, seed=4))
+    outs = [gpu_gradients(nx, ny, S, "fluid", steps, seg, fields) for seg in (1, 9, 13, 90)]
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o[1], outs[0][1])
+        assert o[2] == outs[0][2]
+
+
+def test_rollout_autograd_function_matches_direct_calls():
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9
+    from paper_1312_3297_gb300.autograd import Rollout
+
+    nx, ny, steps = 64, 64, 50
+    fields = f32_fields(inp.noisy_shear_wave(nx, ny, seed=6))
+    rho, ux, uy = fields
+    L, du0, ds, da, _ = gpu_gradients(nx, ny, S, "prescribed", steps, 7, fields, 0.03, 1000.0)
+    sim = D2Q9(nx, ny, S, mode="prescribed")
+    sim.set_utilde(None, 0.03, 1000.0)
+    u0 = torch.tensor(np.stack([ux, uy]), dtype=torch.float32, device="cuda", requires_grad=True)
+    s_nu = torch.tensor(1.9, dtype=torch.float64, requires_grad=True)
+    amp = torch.tensor(0.03, dtype=torch.float64, requires_grad=True)
+    r, u = Rollout.apply(u0, s_nu, amp, sim, steps, 7,
+                         torch.as_tensor(rho, dtype=torch.float32, device="cuda"))
+    loss = 0.5 * (r.double() * (u.double() ** 2).sum(0)).sum()
+    loss.backward()
+    np.testing.assert_allclose(loss.item(), L, rtol=1e-6)
+    np.testing.assert_allclose(u0.grad.double().cpu().numpy(), du0, rtol=2e-5,
+                               atol=2e-5 * np.abs(du0).max())
+    np.testing.assert_allclose(s_nu.grad.item(), ds[4] + ds[5], rtol=2e-5)
+    np.testing.assert_allclose(amp.grad.item(), da, rtol=2e-5)
+    sim.close()
+
+
+def test_adjoint_full_size_1024_2000_steps():
+    """The adjoint workload at full size: 1024^2, 2000 steps, sqrt(N) = 45 checkpoints.
+    The gradient does not depend on the checkpoint interval (bitwise), is finite, and the
+    identity A dL/dA = sum u~0 . dL/du~0 holds."""
+    n, steps = 1024, 2000
+    fields = f32_fields(inp.noisy_shear_wave(n, n, seed=0))
+    a = gpu_gradients(n, n, S, "prescribed", steps, 45, fields, 0.03, 1000.0, field_grad=True)
+    b = gpu_gradients(n, n, S, "prescribed", steps, 400, fields, 0.03, 1000.0)
+    np.testing.assert_array_equal(a[1], b[1])
+    assert a[2] == b[2] and a[3] == b[3]
+    assert np.isfinite(a[1]).all() and np.isfinite(a[2]).all()
+    base = np.stack([np.cos(2 * np.pi * np.arange(n)[:, None] / n) * np.ones((1, n)),
+                     np.sin(2 * np.pi * np.arange(n)[None, :] / n) * np.ones((n, 1))])
+    np.testing.assert_allclose(0.03 * a[3], (base * a[4]).sum(), rtol=1e-4)
