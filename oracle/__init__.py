@@ -11,6 +11,8 @@ Two independent implementations live here:
   taken literally (per-node shifted moment matrix and LU solve), the shifted form of
   Section 1.3 with the T(u~) blocks of Appendix A, and the fixed-moment d'Humieres MRT
   of Section 1.1. This module wraps it with ctypes.
+* ``lbmrv_oracle3d.c`` (wrapped by ``d3q19.py``): the same definition on a D3Q19 lattice
+  with a translation-invariant 19-polynomial basis.
 * ``torch_ref.py`` (plain PyTorch CPU ops in FP64): the same definition written with
   ``torch.linalg.solve`` so that reverse-mode differentiation of the definition gives
   the reference adjoint.
@@ -31,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbmrv_oracle.c")
+_SRCS = [_SRC, os.path.join(_HERE, "lbmrv_oracle3d.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liblbmrv_oracle.so")
 
@@ -51,14 +54,14 @@ def build(force: bool = False) -> str:
     global _openmp
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(p) for p in _SRCS)):
         _openmp = _probe_openmp_flag()
         return _LIB_PATH
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         raise RuntimeError("no C compiler found to build the oracle")
     base = [cc, "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
-            "-fno-fast-math", _SRC, "-o", _LIB_PATH + ".tmp", "-lm"]
+            "-fno-fast-math", *_SRCS, "-o", _LIB_PATH + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True, text=True)
