@@ -202,7 +202,7 @@ def gpu_arm(args):
     size = args.size
     n = size * size
     fields = inp.taylor_green(size, size, u0=0.04)
-    sim = make_sim(torch, D2Q9, inp, "fp32", "prescribed", size, fields)
+    sim = make_sim(torch, D2Q9, inp, args.storage, args.mode, size, fields)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
@@ -230,11 +230,12 @@ def gpu_arm(args):
     sim.close()
     per_step_ms = ms / args.steps
     mlups = world * n * args.steps / (ms * 1e-3) / 1e6
-    achieved = BYTES_PER_NODE["fp32"] * n / (per_step_ms * 1e-3) / 1e9
+    achieved = BYTES_PER_NODE[args.storage] * n / (per_step_ms * 1e-3) / 1e9
+    headline = size == L and args.storage == "fp32" and args.mode == "prescribed"
     out = None
     if rank == 0:
         extras = {}
-        if not args.no_extras and world == 1 and size == L:
+        if not args.no_extras and world == 1 and headline:
             k = max(50, min(args.steps, 300))
             extras["plain_mrt_u0"] = side_measure(torch, D2Q9, inp, "fp32", "zero", L, fields,
                                                   k, peak)
@@ -252,21 +253,26 @@ def gpu_arm(args):
                                                      big, k, peak)
             del big
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
+            extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
         e2e = (e2e_measure(torch, D2Q9, inp, fields, args.steps)
-               if not args.no_e2e and size == L else None)
+               if not args.no_e2e and headline else None)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
         out = {
             "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per_step_ms, 5),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "fp32" else f"{args.storage} storage, f32 math",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD.replace("4096x4096", f"{size}x{size}"), "nodes": n, "bytes_per_node_step": 72,
+            "config": {"workload": WORKLOAD if headline else
+                       f"D2Q9 {args.storage} {size}x{size} Taylor-Green, u~ mode {args.mode}",
+                       "nodes": n, "bytes_per_node_step": BYTES_PER_NODE[args.storage],
                        "l2": "state 1.2 GB > 129 MB L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": recorded_traffic(), "peak_kind": peak_kind,
-                         "kernel": "k_step_vec<float,4,analytic>"},
+                         "traffic": recorded_traffic() if headline else None,
+                         "peak_kind": peak_kind,
+                         "kernel": f"k_step_vec<{args.storage},4,{args.mode}>"},
             "clocks": clock_info,
             "e2e": e2e,
             "gpu_launches": args.steps,
@@ -280,6 +286,29 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def d3q19_measure(torch, inp, steps, peak):
+    """D3Q19 FP32, 256^3 3D Taylor-Green vortex u0 = 0.04, s_nu = 1.7, u~ = q/rho: 152 B per
+    node and step (19 populations read + written)."""
+    from paper_1312_3297_gb300 import D3Q19
+
+    L3 = 256
+    n = L3 ** 3
+    d = inp.taylor_green_3d(L3, L3, L3, u0=0.04)
+    s3 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
+    out = {}
+    for storage, bpn in (("fp32", 152), ("fp16", 76)):
+        sim = D3Q19(L3, L3, L3, s3, mode="fluid", storage=storage)
+        sim.init_equilibrium(torch.as_tensor(d["rho"], dtype=torch.float32),
+                             *(torch.as_tensor(c, dtype=torch.float32) for c in d["u"]))
+        sim.step(3)
+        per = time_steps(sim, steps, torch) / steps
+        sim.close()
+        gbs = bpn * n / (per * 1e-3) / 1e9
+        out[storage] = {"mlups": round(n / (per * 1e-3) / 1e6, 1), "ms_per_step": round(per, 5),
+                        "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    return out
 
 
 def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
@@ -471,6 +500,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--size", type=int, default=L,
                     help="lattice side (a smaller case for profiling captures)")
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"],
+                    help="population storage of the timed run (profiling captures)")
+    ap.add_argument("--mode", default="prescribed", choices=["zero", "fluid", "prescribed"],
+                    help="relative velocity of the timed run (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -25,14 +25,19 @@
  *     lbmrv_set_utilde call).
  *   - Work is enqueued on the handle's CUDA stream and returns without synchronising,
  *     except the calls documented as synchronous (they return host values).
- *   - Lattice layout: periodic D2Q9, dims = {nx, ny, 1}, lattice units dx = 1 (so
- *     dt = 1/lambda, relation (lambda)). Node (x, y) has index i = y*nx + x.
- *     Population state: structure of arrays, 9 planes of nx*ny elements, plane j holds
- *     velocity j in the order (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1)
- *     (times lambda) of Section 1.3. Element i of plane j is at offset j*nx*ny + i.
- *   - Stored value: g_j = f_j - w_j * rho_ref with w = (4/9, 1/9 x4, 1/36 x4), in the
- *     storage type of the handle (FP32, FP16 or BF16, round-to-nearest-even). With
- *     rho_ref = 0 the store holds f itself. All arithmetic is FP32.
+ *   - Lattice layout: periodic D2Q9 (dims = {nx, ny, 1}) or D3Q19 (dims = {nx, ny, nz}),
+ *     lattice units dx = 1 (so dt = 1/lambda, relation (lambda)). Node (x, y, z) has index
+ *     i = (z*ny + y)*nx + x; n = nx*ny*nz. Population state: structure of arrays, q planes
+ *     of n elements (q = 9 or 19); plane j holds velocity j, for D2Q9 in the order
+ *     (0,0),(1,0),(0,1),(-1,0),(0,-1),(1,1),(-1,1),(-1,-1),(1,-1) (times lambda) of Section
+ *     1.3. Element i of plane j is at offset j*n + i. Velocity fields are d planes of n
+ *     floats (d = 2 or 3).
+ *   - Stored value: g_j = f_j - f_eq,j(rho_ref, U_ref), the deviation from the equilibrium
+ *     of a reference state, in the storage type of the handle (FP32, FP16 or BF16,
+ *     round-to-nearest-even). By default U_ref = 0, so g_j = f_j - w_j rho_ref with
+ *     w = (4/9, 1/9 x4, 1/36 x4); rho_ref = 0 stores f itself. lbmrv_set_reference sets a
+ *     reference velocity (useful for 16-bit storage of a flow with a mean velocity). All
+ *     arithmetic is FP32.
  *   - The state kept by the handle after k steps is the POST-relaxation state
  *     S_k = C_k(f(k)) at time k: one lbmrv_step pulls the neighbours' S_{k-1}
  *     (transport) and relaxes at time k. Moments (rho, q) of S_k equal those of f(k),
@@ -65,9 +70,15 @@ extern "C" {
 #define LBMRV_E_TIMEOUT (-5)     /* reserved: no entry point waits on the device */
 #define LBMRV_E_UNSUPPORTED (-6) /* valid request that this build does not implement */
 
-/* Lattices. */
+/* Lattices. D3Q19 uses 19 velocities (0,0,0); (+-1,0,0), (0,+-1,0), (0,0,+-1);
+ * (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0); (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1);
+ * (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1) (times lambda, in this order) and the 19
+ * polynomials 1, X, Y, Z, X^2+Y^2+Z^2, X^2-Y^2, Y^2-Z^2, XY, XZ, YZ, XY^2, XZ^2, YX^2,
+ * YZ^2, ZX^2, ZY^2, X^2Y^2, X^2Z^2, Y^2Z^2 (divided by lambda^degree from degree 2 on).
+ * The paper prints no 3D basis; this one spans a space closed under differentiation, so
+ * its shifting matrix is lower triangular with T(u~)^{-1} = T(-u~), as for D2Q9. */
 #define LBMRV_D2Q9 0
-#define LBMRV_D3Q19 1 /* not built: lbmrv_create returns LBMRV_E_UNSUPPORTED */
+#define LBMRV_D3Q19 1
 
 /* Choice of the relative velocity u~ (Section 1.2, Introduction). */
 #define LBMRV_UT_ZERO 0       /* u~ = 0: d'Humieres MRT */
@@ -84,17 +95,18 @@ typedef struct lbmrv_s* lbmrv_t;
 /* Library version (LBMRV_VERSION). */
 LBMRV_API int lbmrv_version(void);
 
-/* Bytes of one population state (9 * nx * ny * element size) for the given lattice,
- * dims and storage; -1 on invalid arguments. */
+/* Bytes of one population state (q * n * element size) for the given lattice, dims and
+ * storage; -1 on invalid arguments. */
 LBMRV_API int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int storage);
 
 /* Create a simulation handle on the current CUDA device.
- *   lattice  LBMRV_D2Q9.
- *   dims     {nx, ny, 1}, nx, ny >= 1, nx*ny < 2^31.
+ *   lattice  LBMRV_D2Q9 or LBMRV_D3Q19.
+ *   dims     {nx, ny, 1} or {nx, ny, nz}, all >= 1, n < 2^31.
  *   lambda   velocity scale lambda > 0 (relation (lambda)).
- *   s        9 relaxation rates in the moment order of relation (mom): rho, q_x, q_y,
- *            e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps. s[0..2] must be 0 (conserved
- *            moments, Section 1.1); the others are finite.
+ *   s        q relaxation rates in basis order: for D2Q9 the moment order of relation
+ *            (mom): rho, q_x, q_y, e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps; for D3Q19 the
+ *            order of the 3D basis above. The 1 + d conserved rates must be 0 (Section
+ *            1.1); the others are finite.
  *   umode    LBMRV_UT_* (prescribed mode: see lbmrv_set_utilde; default A = 0).
  *   storage  LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16.
  *   rho_ref  reference density of the stored deviation g = f - w rho_ref (0 stores f).
@@ -116,11 +128,18 @@ LBMRV_API int lbmrv_destroy(lbmrv_t h);
  * when h is NULL. Valid until the next call on h. */
 LBMRV_API const char* lbmrv_last_error(lbmrv_t h);
 
+/* Reference state of the stored deviations: g = f - f_eq(rho_ref, u_ref), u_ref = d
+ * doubles in physical units (NULL: zero). Changes how the stored state is read and written, so call it before
+ * lbmrv_init_equilibrium / lbmrv_set_state; an existing state is not converted. The
+ * default is (rho_ref of lbmrv_create, 0, 0). With 16-bit storage a reference velocity
+ * near the mean flow keeps the stored deviations small and their rounding error with them. */
+LBMRV_API int lbmrv_set_reference(lbmrv_t h, double rho_ref, const double* u_ref);
+
 /* Change the stream later work is enqueued on. */
 LBMRV_API int lbmrv_set_stream(lbmrv_t h, void* stream);
 
-/* Kernel variant of the fused step: 0 chooses automatically (the widest aligned pack
- * that divides nx), 1 forces one node per thread (any lattice), 2/4/8 force that many
+/* Kernel variant of the fused step: 0 chooses automatically (the widest aligned pack of
+ * at most 4 nodes that divides nx), 1 forces one node per thread (any lattice), 2/4/8 force that many
  * consecutive nodes per thread with vector loads (must divide nx; at most 4 for FP32,
  * 8 for FP16/BF16; the state buffers must be aligned to the pack). All variants compute
  * the same values; this exists for testing and tuning. */
@@ -128,8 +147,8 @@ LBMRV_API int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread);
 
 /* Prescribed relative velocity u~(x, t) = amplitude * u~0(x) * cos(2 pi t / period),
  * evaluated at the time index t of each relaxation; period <= 0 means no time factor.
- *   ut0_dev  device FP32 [2][nx*ny] (x-component plane then y-component plane), kept
- *            by reference; or NULL for the analytic field u~0 = (cos 2pi y/ny, sin 2pi x/nx).
+ *   ut0_dev  device FP32 [d][n] (one plane per component), kept by reference; or, for
+ *            D2Q9 only, NULL for the analytic field u~0 = (cos 2pi y/ny, sin 2pi x/nx).
  * Only used with LBMRV_UT_PRESCRIBED. */
 LBMRV_API int lbmrv_set_utilde(lbmrv_t h, const float* ut0_dev, double amplitude, double period);
 
@@ -138,8 +157,8 @@ LBMRV_API int lbmrv_set_utilde(lbmrv_t h, const float* ut0_dev, double amplitude
  * second-order polynomial equilibrium (the paper allows any equilibrium independent
  * of u~, Section 1.2). f_eq is a fixed point of the relaxation for every u~, so it is
  * also the post-relaxation state at time 0.
- *   rho_dev  device FP32 [nx*ny], or NULL for rho = 1 everywhere.
- *   u_dev    device FP32 [2][nx*ny] (u_x plane then u_y plane), physical units. */
+ *   rho_dev  device FP32 [n], or NULL for rho = 1 everywhere.
+ *   u_dev    device FP32 [d][n] (one plane per component), physical units. */
 LBMRV_API int lbmrv_init_equilibrium(lbmrv_t h, const float* rho_dev, const float* u_dev);
 
 /* Same from host buffers: copies them into the non-current state buffer on the
@@ -156,17 +175,21 @@ LBMRV_API int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, cons
 LBMRV_API int lbmrv_step(lbmrv_t h, int64_t n);
 
 /* Density and velocity u = q/rho (relation (rhoq)) of the current state.
- *   rho_dev  device FP32 [nx*ny] or NULL;  u_dev  device FP32 [2][nx*ny] or NULL. */
+ *   rho_dev  device FP32 [n] or NULL;  u_dev  device FP32 [d][n] or NULL. */
 LBMRV_API int lbmrv_moments(lbmrv_t h, float* rho_dev, float* u_dev);
 
 /* Same into host buffers; synchronous. Uses the non-current state buffer as staging. */
 LBMRV_API int lbmrv_moments_host(lbmrv_t h, float* rho_host, float* u_host);
 
 /* Global sums of the current state, accumulated in FP64: out_host[0] = sum rho,
- * out_host[1..2] = sum q (physical units), out_host[3] = number of nodes holding a
- * non-finite value. Synchronous. Returns LBMRV_E_NONFINITE (after filling out_host)
+ * out_host[1..2] = sum q_x, sum q_y (physical units), out_host[3] = number of nodes holding
+ * a non-finite value. Synchronous. Returns LBMRV_E_NONFINITE (after filling out_host)
  * when out_host[3] > 0. */
 LBMRV_API int lbmrv_conserved(lbmrv_t h, double out_host[4]);
+
+/* Same for any lattice with all momentum components: out_host = {sum rho, sum q_x,
+ * sum q_y, sum q_z (0 for D2Q9), non-finite nodes}. */
+LBMRV_API int lbmrv_conserved3(lbmrv_t h, double out_host[5]);
 
 /* Copy the current stored state (layout above) to / from a device buffer of
  * lbmrv_state_bytes(). set_state also sets the time index to t. */
@@ -190,7 +213,8 @@ LBMRV_API int lbmrv_set_rates(lbmrv_t h, const double* s);
  * where P^T is a push (the transpose of the pull). J_C^T is the hand-derived transpose of
  * the shifted relaxation (moments, equilibrium moments, T(u~), S, T(-u~), M(0)^{-1}),
  * including the dependence of u~ = q/rho on the populations. Parameter gradients are
- * summed over nodes and steps in FP64. FP32 storage only (else LBMRV_E_UNSUPPORTED).
+ * summed over nodes and steps in FP64. D2Q9 with FP32 storage only (else
+ * LBMRV_E_UNSUPPORTED).
  * Memory: sqrt(N)-style checkpointing. lbmrv_forward_checkpointed stores every seg-th
  * state; lbmrv_adjoint recomputes each segment from its checkpoint (one extra forward in
  * total) and walks it backwards. */
@@ -244,7 +268,9 @@ LBMRV_API int lbmrv_equilibrium_vjp(lbmrv_t h, const float* rho_dev, const float
  * create). Scratch comes from a fixed 38,912-byte array in the library's device image,
  * present on every GPU that loads the library until the process exits.
  *   state_dev  device state in the layout above (9 planes of nx*ny, storage type).
- *   storage    LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16; rho_ref the stored offset.
+ *   storage    LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16; rho_ref the stored offset (the
+ *              state is read with a zero reference velocity; for a state stored with
+ *              lbmrv_set_reference(rho_ref, U), add nx*ny*rho_ref*U to the momentum sums).
  *   dims       {nx, ny, 1}; nx*ny must be below 2^31 (larger sizes: LBMRV_E_INVAL).
  *   out_dev    4 device doubles: sum rho, sum q_x, sum q_y, non-finite node count.
  *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream).

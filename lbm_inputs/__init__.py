@@ -106,3 +106,39 @@ def prescribed_base_field(nx: int, ny: int, seed: int = 0, smooth: bool = True):
         return np.stack([np.sin(TWO_PI * (x / nx + y / ny)), np.cos(TWO_PI * x / nx)])
     rng = np.random.default_rng(seed)
     return rng.standard_normal((2, ny, nx))
+
+
+# ------------------------------------------------------------------ 3D fields (nz, ny, nx)
+def _grid3(nx: int, ny: int, nz: int):
+    z, y, x = np.meshgrid(np.arange(nz, dtype=np.float64), np.arange(ny, dtype=np.float64),
+                          np.arange(nx, dtype=np.float64), indexing="ij")
+    return x, y, z
+
+
+def taylor_green_3d(nx: int, ny: int, nz: int, u0: float = 0.04, rho0: float = 1.0,
+                    lam: float = 1.0):
+    """3D Taylor-Green vortex, k = 2 pi / L per axis:
+    u = u0 (sin kx cos ky cos kz, -cos kx sin ky cos kz, 0),
+    p = rho0 u0^2 / 16 (cos 2kx + cos 2ky)(cos 2kz + 2), rho = rho0 + 3 p / lambda^2.
+    Returns rho (nz, ny, nx) and u (3, nz, ny, nx)."""
+    x, y, z = _grid3(nx, ny, nz)
+    kx, ky, kz = TWO_PI / nx, TWO_PI / ny, TWO_PI / nz
+    ux = u0 * np.sin(kx * x) * np.cos(ky * y) * np.cos(kz * z)
+    uy = -u0 * np.cos(kx * x) * np.sin(ky * y) * np.cos(kz * z)
+    uz = np.zeros_like(ux)
+    p = rho0 * u0 * u0 / 16.0 * (np.cos(2 * kx * x) + np.cos(2 * ky * y)) * (np.cos(2 * kz * z) + 2)
+    return {"rho": rho0 + 3.0 * p / (lam * lam), "u": np.stack([ux, uy, uz])}
+
+
+def random_flow_3d(nx: int, ny: int, nz: int, seed: int = 0, amp: float = 0.04,
+                   u_noise: float = 0.005, rho_noise: float = 0.01):
+    """Small-lattice 3D parity workload: rho = 1 + 0.01 N(0,1), u = amp (sin 2pi y/ny,
+    sin 2pi z/nz, sin 2pi x/nx) + u_noise N(0,1) per component (draws: rho, u_x, u_y, u_z)."""
+    rng = np.random.default_rng(seed)
+    x, y, z = _grid3(nx, ny, nz)
+    rho = 1.0 + rho_noise * rng.standard_normal((nz, ny, nx))
+    noise = [rng.standard_normal((nz, ny, nx)) for _ in range(3)]
+    u = np.stack([amp * np.sin(TWO_PI * y / ny) + u_noise * noise[0],
+                  amp * np.sin(TWO_PI * z / nz) + u_noise * noise[1],
+                  amp * np.sin(TWO_PI * x / nx) + u_noise * noise[2]])
+    return {"rho": rho, "u": u}

@@ -64,6 +64,8 @@ SIGNATURES = [
     ("lbmrv_time", _I64, [_VP]),
     ("lbmrv_conserved_noalloc", _I, [_VP, _I, _I64P, _D, _D, _VP, _VP]),
     ("lbmrv_set_rates", _I, [_VP, _DP]),
+    ("lbmrv_set_reference", _I, [_VP, _D, _DP]),
+    ("lbmrv_conserved3", _I, [_VP, _DP]),
     ("lbmrv_adjoint_workspace_bytes", _I64, [_VP, _I64, _I64]),
     ("lbmrv_forward_checkpointed", _I, [_VP, _I64, _I64, _VP, ctypes.c_size_t]),
     ("lbmrv_adjoint", _I, [_VP, _I64, _I64, _VP, ctypes.c_size_t, _VP, _VP, _DP, _DP, _VP]),
@@ -148,7 +150,7 @@ def lbmrv_state_bytes(lattice: int, dims, storage: int) -> int:
 def lbmrv_create(lattice: int, dims, lam: float, s, umode: int, storage: int,
                  rho_ref: float, stream=None, f_a=None, f_b=None) -> int:
     h = _VP()
-    sv = (ctypes.c_double * 9)(*[float(v) for v in s])
+    sv = (ctypes.c_double * len(s))(*[float(v) for v in s])
     rc = load().lbmrv_create(ctypes.byref(h), lattice, _dims(dims), float(lam), sv, umode,
                              storage, float(rho_ref), _stream(stream), _addr(f_a), _addr(f_b))
     _check(rc, None)
@@ -232,8 +234,22 @@ def lbmrv_conserved_noalloc(state, storage: int, dims, lam: float, rho_ref: floa
 
 
 def lbmrv_set_rates(h, s) -> None:
-    sv = (ctypes.c_double * 9)(*[float(v) for v in s])
+    sv = (ctypes.c_double * len(s))(*[float(v) for v in s])
     _check(load().lbmrv_set_rates(h, sv), h)
+
+
+def lbmrv_set_reference(h, rho_ref: float, u_ref) -> None:
+    u = (ctypes.c_double * 3)(*([float(v) for v in u_ref] + [0.0] * (3 - len(u_ref))))
+    _check(load().lbmrv_set_reference(h, float(rho_ref), u), h)
+
+
+def lbmrv_conserved3(h, allow_nonfinite: bool = False):
+    out = (ctypes.c_double * 5)()
+    rc = load().lbmrv_conserved3(h, out)
+    if rc == LBMRV_E_NONFINITE and allow_nonfinite:
+        return list(out)
+    _check(rc, h)
+    return list(out)
 
 
 def lbmrv_adjoint_workspace_bytes(h, n: int, seg: int) -> int:

@@ -19,21 +19,41 @@ struct Rates {
     float e, pxx, pxy, qx, qy, eps;
 };
 
+// Reference state of the stored deviations g = f - f_eq(rho_ref, U_ref), in lattice
+// units (velocities divided by lambda): rho, the reference momentum j = rho_ref U, the
+// reference velocity U, and c = M(0) f_eq(rho_ref, U) - m_eq(0)(rho_ref, j) + (2 rho_ref,
+// 0, 0, 0, 0, -rho_ref) on the six non-conserved moments, i.e. the constant part of
+// d = m(0) - m_eq(0) once the deviation sums are split off. U = 0 gives j = c = 0.
+struct StoreRef {
+    float rho;
+    float jx, jy;
+    float ux, uy;
+    float c[6];
+};
+
 // Per-launch arguments of the fused step.
 struct StepArgs {
     int nx, ny;
     Rates s;
-    float rho_ref;       // stored value g = f - w rho_ref
+    StoreRef ref;        // stored value g = f - f_eq(ref)
     float amp_t;         // prescribed mode: A cos(2 pi t / P) / lambda at this step
     float two_over_nx;   // 2 / nx, 2 / ny for cospi/sinpi of the analytic field
     float two_over_ny;
     const float* ut0;    // prescribed base field [2][n] or nullptr
-    float sin_k[8];      // sin(2 pi k / nx), cos(2 pi k / nx), k < 8: the analytic field
-    float cos_k[8];      // at x0 + k from its value at x0 by angle addition
+    const float* sin_x;  // sin(2 pi x / nx), x < nx: y-component of the analytic field
 };
 
 // Modes of u~ (kernel template parameter).
 enum { UM_ZERO = 0, UM_FLUID = 1, UM_ANALYTIC = 2, UM_FIELD = 3 };
+
+// Correctly rounded reciprocal (the same value as 1.0f / x, without the division sequence).
+LBMRV_HD float recip(float x) {
+#ifdef __CUDA_ARCH__
+    return __frcp_rn(x);
+#else
+    return 1.0f / x;
+#endif
+}
 
 LBMRV_HD float wgt(int j) {
     return j == 0 ? (4.0f / 9.0f) : (j < 5 ? (1.0f / 9.0f) : (1.0f / 36.0f));
@@ -53,10 +73,11 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float
     return __float2bfloat16_rn(v);
 }
 
-// Moments of one node from stored deviations g (f = g + w rho_ref).
+// Sums of the stored deviations g of one node: rho = rho_ref + drho, q / lambda =
+// j_ref + (jx, jy).
 struct NodeMoments {
-    float drho;  // sum g = rho - rho_ref
-    float jx, jy;  // q / lambda = sum c f = sum c g
+    float drho;  // sum g
+    float jx, jy;  // sum c g
 };
 
 LBMRV_HD NodeMoments node_moments(const float g[9]) {
@@ -77,11 +98,11 @@ LBMRV_HD NodeMoments node_moments(const float g[9]) {
 // of Appendix A. Then f* = f - M(0)^{-1} T(-u~) S T(u~) d, where M(0)^{-1} =
 // M(0)^T diag(1/|row|^2) with |row|^2 = 36, 4, 4, 12, 12, 36 on the six moments.
 LBMRV_HD void relax_node(float g[9], float ux, float uy, const Rates& s,
-                                           float rho_ref) {
+                         const StoreRef& ref) {
     const NodeMoments mo = node_moments(g);
-    const float rho = rho_ref + mo.drho;
-    const float ir = 1.0f / rho;
-    const float jx = mo.jx, jy = mo.jy;
+    const float rho = ref.rho + mo.drho;
+    const float ir = recip(rho);
+    const float jx = ref.jx + mo.jx, jy = ref.jy + mo.jy;
     const float jxx = jx * jx * ir, jyy = jy * jy * ir;
     const float jj3 = 3.0f * (jxx + jyy);
 
@@ -90,14 +111,14 @@ LBMRV_HD void relax_node(float g[9], float ux, float uy, const Rates& s,
     const float a = g[5] - g[7], b = g[6] - g[8];
 
     // d = m(0) - m_eq(0) on the non-conserved moments (Lallemand-Luo equilibrium
-    // moments of the second-order polynomial equilibrium, written for deviations:
-    // M_e w = -2, M_eps w = 1, the other rows of M(0) annihilate w).
-    const float d_e = (-4.0f * g[0] - s1 + 2.0f * s2) + 2.0f * mo.drho - jj3;
-    const float d_pxx = ((g[1] + g[3]) - (g[2] + g[4])) - (jxx - jyy);
-    const float d_pxy = ((g[5] + g[7]) - (g[6] + g[8])) - jx * jy * ir;
-    const float d_qx = (-2.0f * (g[1] - g[3]) + (a - b)) + jx;
-    const float d_qy = (-2.0f * (g[2] - g[4]) + (a + b)) + jy;
-    const float d_eps = (4.0f * g[0] - 2.0f * s1 + s2) - mo.drho + jj3;
+    // moments of the second-order polynomial equilibrium, written for deviations from
+    // the reference state; see StoreRef).
+    const float d_e = (-4.0f * g[0] - s1 + 2.0f * s2) + ref.c[0] + 2.0f * mo.drho - jj3;
+    const float d_pxx = ((g[1] + g[3]) - (g[2] + g[4])) + ref.c[1] - (jxx - jyy);
+    const float d_pxy = ((g[5] + g[7]) - (g[6] + g[8])) + ref.c[2] - jx * jy * ir;
+    const float d_qx = (-2.0f * (g[1] - g[3]) + (a - b)) + ref.c[3] + jx;
+    const float d_qy = (-2.0f * (g[2] - g[4]) + (a + b)) + ref.c[4] + jy;
+    const float d_eps = (4.0f * g[0] - 2.0f * s1 + s2) + ref.c[5] - mo.drho + jj3;
 
     // Shift-block coefficients (Appendix A, blocks C3, D3, D4) at u~/lambda.
     const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
@@ -136,20 +157,20 @@ LBMRV_HD void relax_node(float g[9], float ux, float uy, const Rates& s,
 
 // u~ / lambda at node (x, y) for the compile-time mode.
 template <int UM>
-__device__ __forceinline__ void relative_velocity(const float g[9], float rho_ref, int x, int y,
-                                                  int64_t i, const StepArgs& a, float& ux,
-                                                  float& uy) {
+__device__ __forceinline__ void relative_velocity(const float g[9], const StoreRef& ref, int x,
+                                                  int y, int64_t i, const StepArgs& a,
+                                                  float& ux, float& uy) {
     if (UM == UM_ZERO) {
         ux = 0.0f;
         uy = 0.0f;
     } else if (UM == UM_FLUID) {
         const NodeMoments m = node_moments(g);
-        const float ir = 1.0f / (rho_ref + m.drho);
-        ux = m.jx * ir;
-        uy = m.jy * ir;
+        const float ir = recip(ref.rho + m.drho);
+        ux = (ref.jx + m.jx) * ir;
+        uy = (ref.jy + m.jy) * ir;
     } else if (UM == UM_ANALYTIC) {
         ux = a.amp_t * cospif(a.two_over_ny * (float)y);
-        uy = a.amp_t * sinpif(a.two_over_nx * (float)x);
+        uy = a.amp_t * __ldg(a.sin_x + x);
     } else {
         const int64_t n = (int64_t)a.nx * a.ny;
         ux = a.amp_t * __ldg(a.ut0 + i);

@@ -27,7 +27,7 @@ __device__ __forceinline__ void base_field(int x, int y, int64_t i, const StepAr
                                            float& bx, float& by) {
     if (UM == UM_ANALYTIC) {
         bx = cospif(a.two_over_ny * (float)y);
-        by = sinpif(a.two_over_nx * (float)x);
+        by = __ldg(a.sin_x + x);
     } else if (UM == UM_FIELD) {
         const int64_t n = (int64_t)a.nx * a.ny;
         bx = __ldg(a.ut0 + i);
@@ -103,15 +103,15 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __res
                 base_field<UM>(x, y, i, a, bx, by);
                 if (UM == UM_FLUID) {
                     const NodeMoments m = node_moments(h);
-                    const float ir = 1.0f / (a.rho_ref + m.drho);
-                    ux = m.jx * ir;
-                    uy = m.jy * ir;
+                    const float ir = recip(a.ref.rho + m.drho);
+                    ux = (a.ref.jx + m.jx) * ir;
+                    uy = (a.ref.jy + m.jy) * ir;
                 } else {
                     ux = a.amp_t * bx;
                     uy = a.amp_t * by;
                 }
                 float ubx, uby;
-                relax_node_vjp<UM>(h, ah, ux, uy, a.s, a.rho_ref, o, acc, ubx, uby);
+                relax_node_vjp<UM>(h, ah, ux, uy, a.s, a.ref, o, acc, ubx, uby);
                 if (UM == UM_ANALYTIC || UM == UM_FIELD) {
                     acc[6] += aa.da_factor * (ubx * bx + uby * by);
                     if (aa.dut0) {
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(256) k_acc_final(const double* __restrict__ ac
     }
 }
 
-// Adjoint of the equilibrium initialisation g_j = f_eq,j(rho, u) - w_j rho_ref:
+// Adjoint of the equilibrium initialisation g_j = f_eq,j(rho, u) - f_eq,j(rho_ref, U):
 // dL/drho = sum_j a_j w_j (1 + 3 cu + 9/2 cu^2 - 3/2 |u|^2),
 // dL/du   = sum_j a_j w_j rho (3 c + 9 cu c - 3 u) / lambda, with u in units of lambda.
 __global__ void k_equilibrium_vjp(const float* __restrict__ rho, const float* __restrict__ u,
@@ -200,15 +200,15 @@ __global__ void k_equilibrium_vjp(const float* __restrict__ rho, const float* __
 // dL/dg_j = dL/drho + (lambda / rho) (dL/du . (c_j - j / rho)).
 __global__ void k_moments_vjp(const float* __restrict__ g, const float* __restrict__ drho,
                               const float* __restrict__ du, float* __restrict__ out, int64_t n,
-                              float rho_ref, float lambda) {
+                              StoreRef ref, float lambda) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float h[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) h[j] = g[j * n + i];
         const NodeMoments m = node_moments(h);
-        const float ir = 1.0f / (rho_ref + m.drho);
-        const float ux = m.jx * ir, uy = m.jy * ir;
+        const float ir = recip(ref.rho + m.drho);
+        const float ux = (ref.jx + m.jx) * ir, uy = (ref.jy + m.jy) * ir;
         const float br = drho ? drho[i] : 0.0f;
         const float bx = du ? du[i] * lambda * ir : 0.0f;
         const float by = du ? du[n + i] * lambda * ir : 0.0f;
@@ -225,7 +225,7 @@ __global__ void k_moments_vjp(const float* __restrict__ g, const float* __restri
 // and optionally dL/dg_j = lambda^2 (c_j . j / rho - 1/2 |j|^2 / rho^2).
 __global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const float* __restrict__ g,
                                                                    float* __restrict__ grad,
-                                                                   int64_t n, float rho_ref,
+                                                                   int64_t n, StoreRef ref,
                                                                    float lambda,
                                                                    double* __restrict__ part) {
     float ke = 0.0f;
@@ -238,8 +238,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const float* 
 #pragma unroll
         for (int j = 0; j < 9; ++j) h[j] = g[j * n + i];
         const NodeMoments m = node_moments(h);
-        const float ir = 1.0f / (rho_ref + m.drho);
-        const float jj = m.jx * m.jx + m.jy * m.jy;
+        const float ir = recip(ref.rho + m.drho);
+        const float jx = ref.jx + m.jx, jy = ref.jy + m.jy;
+        const float jj = jx * jx + jy * jy;
         ke += 0.5f * l2 * jj * ir;
         if (++cnt == 64) {  // keep the FP32 run short, accumulate in FP64
             acc += (double)ke;
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const float* 
             for (int j = 0; j < 9; ++j) {
                 const float cx = (float)((j == 1 || j == 5 || j == 8) - (j == 3 || j == 6 || j == 7));
                 const float cy = (float)((j == 2 || j == 5 || j == 6) - (j == 4 || j == 7 || j == 8));
-                grad[j * n + i] = l2 * ((cx * m.jx + cy * m.jy) * ir - 0.5f * jj * ir * ir);
+                grad[j * n + i] = l2 * ((cx * jx + cy * jy) * ir - 0.5f * jj * ir * ir);
             }
         }
     }
@@ -283,6 +284,12 @@ int grid1d(int64_t n, int threads) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+}  // namespace
+
+dim3 adjoint_grid(int nx, int ny, int nv);
+
+namespace {
+
 template <int NV, int UM>
 cudaError_t adjoint_nv_um(const float* s_prev, const float* a_in, bool gather, float* mu_out,
                           const AdjointArgs& aa, cudaStream_t st) {
@@ -309,26 +316,29 @@ cudaError_t adjoint_nv(int um, const float* s_prev, const float* a_in, bool gath
 
 }  // namespace
 
-int adjoint_width(int nx) { return (nx % 4 == 0) ? 4 : 1; }
-
 dim3 adjoint_grid(int nx, int ny, int nv) {
     const int threads_x = (nx / nv + (nx % nv ? 1 : 0));
     return dim3((threads_x + kAdjThreads - 1) / kAdjThreads, ny < 65535 ? ny : 65535);
 }
 
-int64_t adjoint_blocks(int nx, int ny) {
-    const dim3 g = adjoint_grid(nx, ny, adjoint_width(nx));
+int64_t adjoint_blocks(int nx, int ny, int nv) {
+    const dim3 g = adjoint_grid(nx, ny, nv);
     return (int64_t)g.x * g.y;
 }
 
-cudaError_t launch_adjoint_step(int um, const float* s_prev, const float* a_in, bool gather,
-                                float* mu_out, const AdjointArgs& aa, cudaStream_t st) {
-    if (adjoint_width(aa.step.nx) == 4) return adjoint_nv<4>(um, s_prev, a_in, gather, mu_out, aa, st);
-    return adjoint_nv<1>(um, s_prev, a_in, gather, mu_out, aa, st);
+cudaError_t launch_adjoint_step(int um, int nv, const float* s_prev, const float* a_in,
+                                bool gather, float* mu_out, const AdjointArgs& aa,
+                                cudaStream_t st) {
+    switch (nv) {
+        case 4: return adjoint_nv<4>(um, s_prev, a_in, gather, mu_out, aa, st);
+        case 2: return adjoint_nv<2>(um, s_prev, a_in, gather, mu_out, aa, st);
+        case 1: return adjoint_nv<1>(um, s_prev, a_in, gather, mu_out, aa, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_gather(const float* src, float* dst, int nx, int ny, cudaStream_t st) {
-    const int nv = adjoint_width(nx);
+    const int nv = (nx % 4 == 0) ? 4 : 1;
     const dim3 grid = adjoint_grid(nx, ny, nv);
     if (nv == 4)
         k_gather<4><<<grid, kAdjThreads, 0, st>>>(src, dst, nx, ny);
@@ -349,15 +359,15 @@ cudaError_t launch_equilibrium_vjp(const float* rho, const float* u, const float
 }
 
 cudaError_t launch_moments_vjp(const float* g, const float* drho, const float* du, float* out,
-                               int64_t n, float rho_ref, float lambda, cudaStream_t st) {
-    k_moments_vjp<<<grid1d(n, 256), 256, 0, st>>>(g, drho, du, out, n, rho_ref, lambda);
+                               int64_t n, const StoreRef& ref, float lambda, cudaStream_t st) {
+    k_moments_vjp<<<grid1d(n, 256), 256, 0, st>>>(g, drho, du, out, n, ref, lambda);
     return cudaGetLastError();
 }
 
-cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, float rho_ref,
+cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, const StoreRef& ref,
                                   float lambda, double* partials, int nblk, double* out,
                                   cudaStream_t st) {
-    k_kinetic_energy<<<nblk, kReduceThreads, 0, st>>>(g, grad, n, rho_ref, lambda, partials);
+    k_kinetic_energy<<<nblk, kReduceThreads, 0, st>>>(g, grad, n, ref, lambda, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_partials_final<<<1, 32, 0, st>>>(partials, nblk, out);

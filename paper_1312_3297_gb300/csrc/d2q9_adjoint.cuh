@@ -2,7 +2,7 @@
 // relax_node (d2q9.cuh) applied to an adjoint vector, node by node.
 //
 // Forward (per node, deviations g, u = u~/lambda):
-//   rho = rho_ref + sum g, j = sum c g, d = m(0) - m_eq(0) on the six non-conserved
+//   rho = rho_ref + sum g, j = j_ref + sum c g, d = m(0) - m_eq(0) on the six non-conserved
 //   moments, t = T6(u) d, r = S t, h = T6(-u) r, g* = g - M(0)^{-1} h.
 // The reverse sweep below walks these relations backwards (hand-derived), recomputing the
 // forward intermediates in registers. It returns a^T dg*/dg, the per-node contributions to
@@ -31,24 +31,24 @@ LBMRV_HD void mT6(float E, float XX, float XY, float QX, float QY, float EP,
 
 template <int UM>
 LBMRV_HD void relax_node_vjp(const float g[9], const float a[9], float ux,
-                                               float uy, const Rates& s, float rho_ref,
+                                               float uy, const Rates& s, const StoreRef& ref,
                                                float out[9], float sbar[6], float& uxbar,
                                                float& uybar) {
     // ---- forward recompute
     const NodeMoments mo = node_moments(g);
-    const float ir = 1.0f / (rho_ref + mo.drho);
-    const float jx = mo.jx, jy = mo.jy;
+    const float ir = recip(ref.rho + mo.drho);
+    const float jx = ref.jx + mo.jx, jy = ref.jy + mo.jy;
     const float jxx = jx * jx * ir, jyy = jy * jy * ir, pxye = jx * jy * ir;
     const float jj3 = 3.0f * (jxx + jyy);
     const float s1 = (g[1] + g[2]) + (g[3] + g[4]);
     const float s2 = (g[5] + g[6]) + (g[7] + g[8]);
     const float ga = g[5] - g[7], gb = g[6] - g[8];
-    const float d_e = (-4.0f * g[0] - s1 + 2.0f * s2) + 2.0f * mo.drho - jj3;
-    const float d_xx = ((g[1] + g[3]) - (g[2] + g[4])) - (jxx - jyy);
-    const float d_xy = ((g[5] + g[7]) - (g[6] + g[8])) - pxye;
-    const float d_qx = (-2.0f * (g[1] - g[3]) + (ga - gb)) + jx;
-    const float d_qy = (-2.0f * (g[2] - g[4]) + (ga + gb)) + jy;
-    const float d_ep = (4.0f * g[0] - 2.0f * s1 + s2) - mo.drho + jj3;
+    const float d_e = (-4.0f * g[0] - s1 + 2.0f * s2) + ref.c[0] + 2.0f * mo.drho - jj3;
+    const float d_xx = ((g[1] + g[3]) - (g[2] + g[4])) + ref.c[1] - (jxx - jyy);
+    const float d_xy = ((g[5] + g[7]) - (g[6] + g[8])) + ref.c[2] - pxye;
+    const float d_qx = (-2.0f * (g[1] - g[3]) + (ga - gb)) + ref.c[3] + jx;
+    const float d_qy = (-2.0f * (g[2] - g[4]) + (ga + gb)) + ref.c[4] + jy;
+    const float d_ep = (4.0f * g[0] - 2.0f * s1 + s2) + ref.c[5] - mo.drho + jj3;
     const float ux2 = ux * ux, uy2 = uy * uy, uxy = ux * uy;
     const float d3e = 6.0f * (ux2 + uy2), d3xx = 9.0f * (ux2 - uy2), d3xy = 36.0f * uxy;
     const float t_qx = d_qx - 2.0f * ux * d_e - 3.0f * ux * d_xx - 6.0f * uy * d_xy;

@@ -38,8 +38,8 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
         g[7] = to_f(src[7 * n + rp + xp]);
         g[8] = to_f(src[8 * n + rp + xm]);
         float ux, uy;
-        relative_velocity<UM>(g, a.rho_ref, x, y, r0 + x, a, ux, uy);
-        relax_node(g, ux, uy, a.s, a.rho_ref);
+        relative_velocity<UM>(g, a.ref, x, y, r0 + x, a, ux, uy);
+        relax_node(g, ux, uy, a.s, a.ref);
 #pragma unroll
         for (int j = 0; j < 9; ++j) dst[j * n + r0 + x] = from_f<T>(g[j]);
     }
@@ -61,11 +61,12 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
         float g[9][NV];
         pull_pack<T, NV>(src, n, r0, rm, rp, p, g);
         if (p.act) {
-            // analytic prescribed field: one sincospi per thread, then angle addition
-            float ux_row = 0.0f, s0 = 0.0f, c0 = 0.0f;
+            // analytic prescribed field: cos 2 pi y/ny once per row, sin 2 pi x/nx from a
+            // per-column table (one vector load per pack, served by L1/L2)
+            float ux_row = 0.0f, sx[NV];
             if (UM == UM_ANALYTIC) {
                 ux_row = a.amp_t * cospif(a.two_over_ny * (float)y);
-                sincospif(a.two_over_nx * (float)p.x0, &s0, &c0);
+                load_pack<float, NV>(a.sin_x + p.x0, true, sx);
             }
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
@@ -75,11 +76,11 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                 float ux, uy;
                 if (UM == UM_ANALYTIC) {
                     ux = ux_row;
-                    uy = a.amp_t * (s0 * a.cos_k[k] + c0 * a.sin_k[k]);
+                    uy = a.amp_t * sx[k];
                 } else {
-                    relative_velocity<UM>(h, a.rho_ref, p.x0 + k, y, r0 + p.x0 + k, a, ux, uy);
+                    relative_velocity<UM>(h, a.ref, p.x0 + k, y, r0 + p.x0 + k, a, ux, uy);
                 }
-                relax_node(h, ux, uy, a.s, a.rho_ref);
+                relax_node(h, ux, uy, a.s, a.ref);
 #pragma unroll
                 for (int j = 0; j < 9; ++j) g[j][k] = h[j];
             }
@@ -90,14 +91,15 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
 }
 
 // --------------------------------------------------------------------------------------
-// Equilibrium initialisation: g_j = f_eq,j(rho, u) - w_j rho_ref, written as
-// w_j (rho - rho_ref) + w_j rho (3 c.u + 9/2 (c.u)^2 - 3/2 |u|^2) with u in units of lambda.
+// Equilibrium initialisation: g_j = f_eq,j(rho, u) - f_eq,j(rho_ref, U), written as
+// w_j (rho - rho_ref) + w_j (rho P_j(u) - rho_ref P_j(U)), P_j(v) = 3 c.v + 9/2 (c.v)^2
+// - 3/2 |v|^2, velocities in units of lambda.
 __constant__ int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __constant__ int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 
 template <typename T>
 __global__ void k_init_eq(T* __restrict__ dst, const float* __restrict__ rho,
-                          const float* __restrict__ u, int64_t n, float rho_ref,
+                          const float* __restrict__ u, int64_t n, StoreRef ref,
                           float inv_lambda) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -105,12 +107,16 @@ __global__ void k_init_eq(T* __restrict__ dst, const float* __restrict__ rho,
         const float ux = u ? u[i] * inv_lambda : 0.0f;
         const float uy = u ? u[n + i] * inv_lambda : 0.0f;
         const float uu = ux * ux + uy * uy;
-        const float dr = r - rho_ref;
+        const float UU = ref.ux * ref.ux + ref.uy * ref.uy;
+        const float dr = r - ref.rho;
 #pragma unroll
         for (int j = 0; j < 9; ++j) {
             const float cu = (float)kCX[j] * ux + (float)kCY[j] * uy;
+            const float cU = (float)kCX[j] * ref.ux + (float)kCY[j] * ref.uy;
             const float w = wgt(j);
-            dst[j * n + i] = from_f<T>(w * dr + w * r * (3.0f * cu + 4.5f * cu * cu - 1.5f * uu));
+            const float pu = 3.0f * cu + 4.5f * cu * cu - 1.5f * uu;
+            const float pU = 3.0f * cU + 4.5f * cU * cU - 1.5f * UU;
+            dst[j * n + i] = from_f<T>(w * dr + w * (r * pu - ref.rho * pU));
         }
     }
 }
@@ -118,24 +124,24 @@ __global__ void k_init_eq(T* __restrict__ dst, const float* __restrict__ rho,
 // Density and velocity (relation (rhoq)) of the stored state.
 template <typename T>
 __global__ void k_moments(const T* __restrict__ src, float* __restrict__ rho,
-                          float* __restrict__ u, int64_t n, float rho_ref, float lambda) {
+                          float* __restrict__ u, int64_t n, StoreRef ref, float lambda) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         float g[9];
 #pragma unroll
         for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * n + i]);
         const NodeMoments m = node_moments(g);
-        const float r = rho_ref + m.drho;
+        const float r = ref.rho + m.drho;
         if (rho) rho[i] = r;
         if (u) {
-            u[i] = lambda * m.jx / r;
-            u[n + i] = lambda * m.jy / r;
+            u[i] = lambda * (ref.jx + m.jx) / r;
+            u[n + i] = lambda * (ref.jy + m.jy) / r;
         }
     }
 }
 
 // --------------------------------------------------------------------------------------
-// FP64 sums of (rho - rho_ref, q_x / lambda, q_y / lambda, non-finite nodes): per-node
+// FP64 sums of the deviations (sum g, sum c g, non-finite nodes): per-node
 // FP32 moments accumulated in FP64 per thread, warp-shuffle and shared-memory tree per
 // block, one partial per block; a second one-block kernel adds the partials in a fixed
 // order, so the result is deterministic.
@@ -201,6 +207,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* _
 
 __global__ void __launch_bounds__(kReduceThreads) k_conserved_final(const double* __restrict__ part,
                                                                     int nblk, double rho_ref_n,
+                                                                    double jx_ref_n,
+                                                                    double jy_ref_n,
                                                                     double lambda,
                                                                     double* __restrict__ out) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
@@ -213,8 +221,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_final(const double
     __syncthreads();
     if (threadIdx.x == 0) {
         out[0] = res[0] + rho_ref_n;
-        out[1] = lambda * res[1];
-        out[2] = lambda * res[2];
+        out[1] = lambda * (res[1] + jx_ref_n);
+        out[2] = lambda * (res[2] + jy_ref_n);
         out[3] = res[3];
     }
 }
@@ -268,10 +276,9 @@ cudaError_t step_dispatch_um(const void* src, void* dst, const StepArgs& a, cuda
 }  // namespace
 
 int step_vector_width(int storage, int nx) {
-    // Widest pack of at most 4 nodes that divides nx: 16-byte packs for FP32, 8-byte packs
-    // for the 16-bit types (8-node packs need ~120 registers and ran slower on GB300).
-    const int widest = 4;
-    (void)storage;
+    // Widest pack that divides nx: 16-byte packs, i.e. 4 nodes for FP32 and 8 for the
+    // 16-bit types (measured fastest on GB300 with pairwise 16-bit conversions).
+    const int widest = storage == kStoreF32 ? 4 : 8;
     for (int nv = widest; nv > 1; nv >>= 1)
         if (nx % nv == 0 && nx >= nv) return nv;
     return 1;
@@ -288,7 +295,7 @@ cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
 }
 
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
-                           float rho_ref, float inv_lambda, cudaStream_t st) {
+                           const StoreRef& rho_ref, float inv_lambda, cudaStream_t st) {
     const int g = grid_for(n, 256);
     switch (storage) {
         case kStoreF32:
@@ -309,7 +316,7 @@ cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float
 }
 
 cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, int64_t n,
-                           float rho_ref, float lambda, cudaStream_t st) {
+                           const StoreRef& rho_ref, float lambda, cudaStream_t st) {
     const int g = grid_for(n, 256);
     switch (storage) {
         case kStoreF32:
@@ -335,8 +342,8 @@ int conserved_blocks(int64_t n) {
 }
 
 cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho_ref,
-                             double lambda, double* partials, int nblk, double* out,
-                             cudaStream_t st) {
+                             double jx_ref, double jy_ref, double lambda, double* partials,
+                             int nblk, double* out, cudaStream_t st) {
     switch (storage) {
         case kStoreF32:
             k_conserved_partial<float><<<nblk, kReduceThreads, 0, st>>>(
@@ -354,8 +361,9 @@ cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_conserved_final<<<1, kReduceThreads, 0, st>>>(partials, nblk, rho_ref * (double)n, lambda,
-                                                    out);
+    k_conserved_final<<<1, kReduceThreads, 0, st>>>(partials, nblk, rho_ref * (double)n,
+                                                    jx_ref * (double)n, jy_ref * (double)n,
+                                                    lambda, out);
     return cudaGetLastError();
 }
 

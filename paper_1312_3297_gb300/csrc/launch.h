@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "d2q9.cuh"
+#include "d3q19.cuh"
 
 namespace lbmrv {
 
@@ -22,17 +23,31 @@ cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
                         const StepArgs& a, cudaStream_t st);
 
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
-                           float rho_ref, float inv_lambda, cudaStream_t st);
+                           const StoreRef& ref, float inv_lambda, cudaStream_t st);
 
 cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, int64_t n,
-                           float rho_ref, float lambda, cudaStream_t st);
+                           const StoreRef& ref, float lambda, cudaStream_t st);
 
 int conserved_blocks(int64_t n);
 
-// partials: 4 * nblk doubles of scratch; out: 4 doubles (device).
+// partials: 4 * nblk doubles of scratch; out: 4 doubles (device). rho_ref, jx_ref, jy_ref:
+// the stored reference state (jx_ref = rho_ref U_x / lambda).
 cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho_ref,
-                             double lambda, double* partials, int nblk, double* out,
-                             cudaStream_t st);
+                             double jx_ref, double jy_ref, double lambda, double* partials,
+                             int nblk, double* out, cudaStream_t st);
+
+// ---------------------------------------------------------------- D3Q19
+int step3_vector_width(int nx);
+cudaError_t launch_step3(int storage, int um, int nv, const void* src, void* dst,
+                         const StepArgs3& a, cudaStream_t st);
+cudaError_t launch_init_eq3(int storage, void* dst, const float* rho, const float* u, int64_t n,
+                            const StoreRef3& ref, float inv_lambda, cudaStream_t st);
+cudaError_t launch_moments3(int storage, const void* src, float* rho, float* u, int64_t n,
+                            const StoreRef3& ref, float lambda, cudaStream_t st);
+// partials: 8 * nblk doubles; out: 5 doubles (sum rho, sum q (3), non-finite nodes).
+cudaError_t launch_conserved3(int storage, const void* src, int64_t n, const StoreRef3& ref,
+                              double lambda, double* partials, int nblk, double* out,
+                              cudaStream_t st);
 
 // ---------------------------------------------------------------- adjoint (FP32 state)
 struct AdjointArgs {
@@ -42,21 +57,22 @@ struct AdjointArgs {
     double* acc;       // per-block FP64 accumulators, 8 per block (6 rates, dL/dA, unused)
 };
 
-int adjoint_width(int nx);
 dim3 adjoint_grid(int nx, int ny, int nv);
-int64_t adjoint_blocks(int nx, int ny);
+int64_t adjoint_blocks(int nx, int ny, int nv);
 
-// mu_out = J_C(P s_prev)^T a, a = (gather ? P^T a_in : a_in); accumulates into aa.acc.
-cudaError_t launch_adjoint_step(int um, const float* s_prev, const float* a_in, bool gather,
-                                float* mu_out, const AdjointArgs& aa, cudaStream_t st);
+// mu_out = J_C(P s_prev)^T a, a = (gather ? P^T a_in : a_in); accumulates into aa.acc;
+// nv nodes per thread (1, 2 or 4, dividing nx unless 1).
+cudaError_t launch_adjoint_step(int um, int nv, const float* s_prev, const float* a_in,
+                                bool gather, float* mu_out, const AdjointArgs& aa,
+                                cudaStream_t st);
 cudaError_t launch_gather(const float* src, float* dst, int nx, int ny, cudaStream_t st);
 cudaError_t launch_acc_final(const double* acc, int64_t nblk, double* out, cudaStream_t st);
 cudaError_t launch_equilibrium_vjp(const float* rho, const float* u, const float* a, float* drho,
                                    float* du, int64_t n, float inv_lambda, cudaStream_t st);
 cudaError_t launch_moments_vjp(const float* g, const float* drho, const float* du, float* out,
-                               int64_t n, float rho_ref, float lambda, cudaStream_t st);
+                               int64_t n, const StoreRef& ref, float lambda, cudaStream_t st);
 // partials: 4 * nblk doubles of scratch (slot 0 of each used); out: 1 double (device).
-cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, float rho_ref,
+cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, const StoreRef& ref,
                                   float lambda, double* partials, int nblk, double* out,
                                   cudaStream_t st);
 

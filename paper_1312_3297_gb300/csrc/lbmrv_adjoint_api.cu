@@ -22,12 +22,19 @@ struct WsLayout {
     size_t state = 0, off_seg = 0, off_mu = 0, off_acc = 0, total = 0;
 };
 
+// Nodes per thread of the adjoint kernel: the handle's kernel width when it is 1, 2 or 4,
+// else 4 when it divides nx, else 1.
+int adjoint_nv(const lbmrv_s* h) {
+    if (h->width == 1 || h->width == 2 || h->width == 4) return h->width;
+    return h->nx % 4 == 0 ? 4 : 1;
+}
+
 WsLayout layout(const lbmrv_s* h, int64_t n, int64_t seg) {
     WsLayout L;
     L.seg = seg;
     L.C = (n + seg - 1) / seg;
     L.state = round_up((size_t)(9 * h->n) * sizeof(float));
-    L.nblk = adjoint_blocks((int)h->nx, (int)h->ny);
+    L.nblk = adjoint_blocks((int)h->nx, (int)h->ny, adjoint_nv(h));
     L.off_seg = (size_t)L.C * L.state;
     L.off_mu = L.off_seg + (size_t)(seg - 1) * L.state;
     L.off_acc = L.off_mu + 2 * L.state;
@@ -38,8 +45,8 @@ WsLayout layout(const lbmrv_s* h, int64_t n, int64_t seg) {
 int check_common(lbmrv_t h, int64_t n, int64_t seg, const void* ws, size_t ws_bytes,
                  const char* who, WsLayout* out) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "%s: NULL handle", who);
-    if (h->storage != LBMRV_FP32)
-        return fail(h, LBMRV_E_UNSUPPORTED, "%s: the adjoint needs FP32 storage", who);
+    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "%s: the adjoint needs a D2Q9 FP32 handle", who);
     if (n < 1 || seg < 1 || seg > n)
         return fail(h, LBMRV_E_INVAL, "%s: need n >= 1 and 1 <= seg <= n", who);
     if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign)
@@ -59,7 +66,7 @@ char* at(void* ws, size_t off) { return static_cast<char*>(ws) + off; }
 extern "C" {
 
 int64_t lbmrv_adjoint_workspace_bytes(lbmrv_t h, int64_t n, int64_t seg) {
-    if (!h || n < 1 || seg < 1 || seg > n) return -1;
+    if (!h || n < 1 || seg < 1 || seg > n || h->lattice != LBMRV_D2Q9) return -1;
     return (int64_t)layout(h, n, seg).total;
 }
 
@@ -70,14 +77,12 @@ int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
     if (rc != LBMRV_OK) return rc;
     DeviceGuard g(h->device);
     const size_t bytes = (size_t)(9 * h->n) * sizeof(float);
-    const int um = kernel_mode(h);
     const int nv = choose_width(h, h->f[0], h->f[1]);
     const int64_t t0 = h->t;
     cudaError_t e = cudaMemcpyAsync(at(ws_dev, 0), h->f[h->cur], bytes, cudaMemcpyDeviceToDevice,
                                     h->stream);
     for (int64_t k = 1; k <= n && e == cudaSuccess; ++k) {
-        e = launch_step(h->storage, um, nv, h->f[h->cur], h->f[1 - h->cur], make_args(h, t0 + k),
-                        h->stream);
+        e = launch_handle_step(h, nv, h->f[h->cur], h->f[1 - h->cur], t0 + k);
         h->cur = 1 - h->cur;
         h->t = t0 + k;
         if (e == cudaSuccess && k % seg == 0 && k < n)
@@ -111,6 +116,7 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
     const int64_t t0 = h->ckpt_t0;
     const int um = kernel_mode(h);
     const int nv = choose_width(h, ws_dev, ws_dev);
+    const int anv = adjoint_nv(h);
     double* acc = reinterpret_cast<double*>(at(ws_dev, L.off_acc));
     double* res = acc + 8 * L.nblk;
     float* mu[2] = {reinterpret_cast<float*>(at(ws_dev, L.off_mu)),
@@ -140,7 +146,7 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
             aa.da_factor = (float)(time_factor(h, t0 + k) / h->lambda);
             aa.dut0 = dL_dut0_dev;
             aa.acc = acc;
-            e = launch_adjoint_step(um, s_prev, a, gather, mu[pp], aa, h->stream);
+            e = launch_adjoint_step(um, anv, s_prev, a, gather, mu[pp], aa, h->stream);
             a = mu[pp];
             gather = true;
             pp ^= 1;
@@ -163,12 +169,12 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
 
 int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
     if (!h || !ke_host) return fail(h, LBMRV_E_INVAL, "lbmrv_kinetic_energy: NULL argument");
-    if (h->storage != LBMRV_FP32)
-        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_kinetic_energy: needs FP32 storage");
+    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_kinetic_energy: needs a D2Q9 FP32 handle");
     DeviceGuard g(h->device);
-    double* res = h->red + 4 * (size_t)h->red_blocks;
+    double* res = h->red + 8 * (size_t)h->red_blocks;
     cudaError_t e = launch_kinetic_energy(static_cast<const float*>(h->f[h->cur]), dL_dS_dev, h->n,
-                                          (float)h->rho_ref, (float)h->lambda, h->red,
+                                          store_ref(h), (float)h->lambda, h->red,
                                           h->red_blocks, res, h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ke_host, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
@@ -180,11 +186,11 @@ int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
 int lbmrv_moments_vjp(lbmrv_t h, const float* dL_drho_dev, const float* dL_du_dev,
                       float* dL_dS_dev) {
     if (!h || !dL_dS_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_moments_vjp: NULL argument");
-    if (h->storage != LBMRV_FP32)
-        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_moments_vjp: needs FP32 storage");
+    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_moments_vjp: needs a D2Q9 FP32 handle");
     DeviceGuard g(h->device);
     cudaError_t e = launch_moments_vjp(static_cast<const float*>(h->f[h->cur]), dL_drho_dev,
-                                       dL_du_dev, dL_dS_dev, h->n, (float)h->rho_ref,
+                                       dL_du_dev, dL_dS_dev, h->n, store_ref(h),
                                        (float)h->lambda, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_moments_vjp");
     return LBMRV_OK;
@@ -194,6 +200,8 @@ int lbmrv_equilibrium_vjp(lbmrv_t h, const float* rho_dev, const float* u_dev,
                           const float* dL_dS0_dev, float* dL_drho_dev, float* dL_du_dev) {
     if (!h || !u_dev || !dL_dS0_dev)
         return fail(h, LBMRV_E_INVAL, "lbmrv_equilibrium_vjp: NULL argument");
+    if (h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_equilibrium_vjp: needs a D2Q9 handle");
     DeviceGuard g(h->device);
     cudaError_t e = launch_equilibrium_vjp(rho_dev, u_dev, dL_dS0_dev, dL_drho_dev, dL_du_dev, h->n,
                                            (float)(1.0 / h->lambda), h->stream);

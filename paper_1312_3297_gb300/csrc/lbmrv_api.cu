@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "handle.h"
 #include "launch.h"
@@ -17,6 +18,22 @@ namespace lbmrv {
 
 namespace {
 thread_local char g_create_err[320] = {0};
+
+int lattice_q(int lattice) { return lattice == LBMRV_D2Q9 ? 9 : (lattice == LBMRV_D3Q19 ? 19 : -1); }
+int lattice_dim(int lattice) { return lattice == LBMRV_D2Q9 ? 2 : 3; }
+
+// Validation shared by lbmrv_create and lbmrv_set_rates: conserved rates are 0 (Section
+// 1.1: 1 + d conserved moments), the others finite.
+int check_rates(lbmrv_t h, int lattice, const double* s, const char* who) {
+    const int q = lattice_q(lattice), nc = 1 + lattice_dim(lattice);
+    if (!s) return fail(h, LBMRV_E_INVAL, "%s: s is NULL", who);
+    for (int k = 0; k < nc; ++k)
+        if (s[k] != 0.0)
+            return fail(h, LBMRV_E_INVAL, "%s: s[%d] must be 0 (conserved moment)", who, k);
+    for (int k = nc; k < q; ++k)
+        if (!std::isfinite(s[k])) return fail(h, LBMRV_E_INVAL, "%s: s[%d] is not finite", who, k);
+    return LBMRV_OK;
+}
 }  // namespace
 
 int fail(lbmrv_t h, int code, const char* fmt, ...) {
@@ -28,9 +45,12 @@ int fail(lbmrv_t h, int code, const char* fmt, ...) {
     return code;
 }
 
+const char* last_create_error() { return g_create_err; }
+
 int choose_width(const lbmrv_s* h, const void* a, const void* b) {
     if (h->width > 0) return h->width;
-    const int nv = step_vector_width(h->storage, (int)h->nx);
+    const int nv = h->lattice == LBMRV_D2Q9 ? step_vector_width(h->storage, (int)h->nx)
+                                            : step3_vector_width((int)h->nx);
     const size_t align = (size_t)(nv * elem_size(h->storage));
     if (nv > 1 && ((reinterpret_cast<uintptr_t>(a) % align) != 0 ||
                    (reinterpret_cast<uintptr_t>(b) % align) != 0))
@@ -38,7 +58,11 @@ int choose_width(const lbmrv_s* h, const void* a, const void* b) {
     return nv;
 }
 
-const char* last_create_error() { return g_create_err; }
+cudaError_t launch_handle_step(const lbmrv_s* h, int nv, const void* src, void* dst, int64_t t) {
+    if (h->lattice == LBMRV_D2Q9)
+        return launch_step(h->storage, kernel_mode(h), nv, src, dst, make_args(h, t), h->stream);
+    return launch_step3(h->storage, kernel_mode(h), nv, src, dst, make_args3(h, t), h->stream);
+}
 
 }  // namespace lbmrv
 
@@ -47,10 +71,13 @@ extern "C" {
 int lbmrv_version(void) { return LBMRV_VERSION; }
 
 int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int storage) {
-    if (lattice != LBMRV_D2Q9 || !dims || dims[0] < 1 || dims[1] < 1) return -1;
+    const int q = lattice_q(lattice);
+    if (q < 0 || !dims || dims[0] < 1 || dims[1] < 1) return -1;
+    const int64_t nz = lattice == LBMRV_D3Q19 ? dims[2] : 1;
+    if (nz < 1) return -1;
     const int64_t es = elem_size(storage);
     if (es < 0) return -1;
-    return 9 * dims[0] * dims[1] * es;
+    return q * dims[0] * dims[1] * nz * es;
 }
 
 int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda,
@@ -58,23 +85,22 @@ int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda
                  void* f_a_dev, void* f_b_dev) {
     if (!out) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: out is NULL");
     *out = nullptr;
-    if (lattice == LBMRV_D3Q19)
-        return fail(nullptr, LBMRV_E_UNSUPPORTED, "lbmrv_create: D3Q19 is not built");
-    if (lattice != LBMRV_D2Q9) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: bad lattice");
-    if (!dims || dims[0] < 1 || dims[1] < 1 || (dims[2] != 1 && dims[2] != 0))
-        return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: dims must be {nx>=1, ny>=1, 1}");
-    if (dims[0] * dims[1] >= (int64_t(1) << 31) || dims[0] > (1 << 30) || dims[1] > (1 << 30))
-        return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: nx*ny must be below 2^31");
+    const int q = lattice_q(lattice);
+    if (q < 0) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: bad lattice");
+    if (!dims || dims[0] < 1 || dims[1] < 1)
+        return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: dims must be >= 1");
+    if (lattice == LBMRV_D2Q9 && dims[2] != 1 && dims[2] != 0)
+        return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: D2Q9 dims must be {nx>=1, ny>=1, 1}");
+    if (lattice == LBMRV_D3Q19 && dims[2] < 1)
+        return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: D3Q19 dims must be >= 1");
+    const int64_t nz = lattice == LBMRV_D3Q19 ? dims[2] : 1;
+    if (dims[0] > (1 << 30) || dims[1] > (1 << 30) || nz > (1 << 30) ||
+        dims[0] * dims[1] * nz >= (int64_t(1) << 31))
+        return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: the node count must be below 2^31");
     if (!(lambda > 0.0) || !std::isfinite(lambda))
         return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: lambda must be finite and > 0");
-    if (!s) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: s is NULL");
-    for (int k = 0; k < 3; ++k)
-        if (s[k] != 0.0)
-            return fail(nullptr, LBMRV_E_INVAL,
-                        "lbmrv_create: s[%d] must be 0 (conserved moment)", k);
-    for (int k = 3; k < 9; ++k)
-        if (!std::isfinite(s[k]))
-            return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: s[%d] is not finite", k);
+    int rc = check_rates(nullptr, lattice, s, "lbmrv_create");
+    if (rc != LBMRV_OK) return rc;
     if (umode < LBMRV_UT_ZERO || umode > LBMRV_UT_PRESCRIBED)
         return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: bad u~ mode %d", umode);
     if (elem_size(storage) < 0)
@@ -91,14 +117,17 @@ int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda
     lbmrv_s* h = new (std::nothrow) lbmrv_s();
     if (!h) return fail(nullptr, LBMRV_E_NOMEM, "lbmrv_create: host allocation failed");
     h->lattice = lattice;
+    h->q = q;
+    h->dim = lattice_dim(lattice);
     h->umode = umode;
     h->storage = storage;
     h->nx = dims[0];
     h->ny = dims[1];
-    h->n = dims[0] * dims[1];
+    h->nz = nz;
+    h->n = dims[0] * dims[1] * nz;
     h->lambda = lambda;
     h->rho_ref = rho_ref;
-    for (int k = 0; k < 9; ++k) h->s[k] = s[k];
+    for (int k = 0; k < q; ++k) h->s[k] = s[k];
     h->stream = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaGetDevice(&h->device);
     if (e != cudaSuccess) {
@@ -106,30 +135,36 @@ int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda
         return fail(nullptr, LBMRV_E_CUDA, "lbmrv_create: cudaGetDevice: %s",
                     cudaGetErrorString(e));
     }
-    const size_t bytes = (size_t)lbmrv_state_bytes(lattice, dims, storage);
+    const size_t bytes = state_bytes(h);
+    bool ok = true;
     if (f_a_dev) {
         h->f[0] = f_a_dev;
         h->f[1] = f_b_dev;
     } else {
         h->owns_f = true;
-        if (cudaMalloc(&h->f[0], bytes) != cudaSuccess ||
-            cudaMalloc(&h->f[1], bytes) != cudaSuccess) {
-            cudaGetLastError();
-            if (h->f[0]) cudaFree(h->f[0]);
-            delete h;
-            return fail(nullptr, LBMRV_E_NOMEM, "lbmrv_create: cudaMalloc of 2 x %zu bytes failed",
-                        bytes);
-        }
+        ok = cudaMalloc(&h->f[0], bytes) == cudaSuccess && cudaMalloc(&h->f[1], bytes) == cudaSuccess;
     }
     h->red_blocks = conserved_blocks(h->n);
-    if (cudaMalloc(&h->red, sizeof(double) * (4 * (size_t)h->red_blocks + 4)) != cudaSuccess) {
+    ok = ok && cudaMalloc(&h->red, sizeof(double) * (8 * (size_t)h->red_blocks + 8)) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->sin_x, sizeof(float) * (size_t)h->nx) == cudaSuccess;
+    if (ok) {
+        std::vector<float> tab((size_t)h->nx);
+        for (int64_t x = 0; x < h->nx; ++x)
+            tab[(size_t)x] = (float)std::sin(2.0 * M_PI * (double)x / (double)h->nx);
+        ok = cudaMemcpy(h->sin_x, tab.data(), sizeof(float) * tab.size(),
+                        cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
         cudaGetLastError();
         if (h->owns_f) {
             cudaFree(h->f[0]);
             cudaFree(h->f[1]);
         }
+        cudaFree(h->red);
+        cudaFree(h->sin_x);
         delete h;
-        return fail(nullptr, LBMRV_E_NOMEM, "lbmrv_create: reduction buffer allocation failed");
+        return fail(nullptr, LBMRV_E_NOMEM, "lbmrv_create: device allocation of %zu bytes failed",
+                    2 * bytes);
     }
     *out = h;
     return LBMRV_OK;
@@ -144,6 +179,7 @@ int lbmrv_destroy(lbmrv_t h) {
         cudaFree(h->f[1]);
     }
     cudaFree(h->red);
+    cudaFree(h->sin_x);
     delete h;
     return LBMRV_OK;
 }
@@ -163,7 +199,7 @@ int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread) {
         h->width = w;
         return LBMRV_OK;
     }
-    const int widest = h->storage == LBMRV_FP32 ? 4 : 8;
+    const int widest = h->lattice == LBMRV_D3Q19 ? 4 : (h->storage == LBMRV_FP32 ? 4 : 8);
     if ((w != 2 && w != 4 && w != 8) || w > widest || h->nx % w != 0)
         return fail(h, LBMRV_E_INVAL,
                     "lbmrv_set_kernel_width: %d must be 0, 1 or a pack width (<= %d) dividing nx",
@@ -177,14 +213,21 @@ int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread) {
 
 int lbmrv_set_rates(lbmrv_t h, const double* s) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_rates: NULL handle");
-    if (!s) return fail(h, LBMRV_E_INVAL, "lbmrv_set_rates: s is NULL");
-    for (int k = 0; k < 3; ++k)
-        if (s[k] != 0.0)
-            return fail(h, LBMRV_E_INVAL, "lbmrv_set_rates: s[%d] must be 0 (conserved moment)", k);
-    for (int k = 3; k < 9; ++k)
-        if (!std::isfinite(s[k]))
-            return fail(h, LBMRV_E_INVAL, "lbmrv_set_rates: s[%d] is not finite", k);
-    for (int k = 0; k < 9; ++k) h->s[k] = s[k];
+    int rc = check_rates(h, h->lattice, s, "lbmrv_set_rates");
+    if (rc != LBMRV_OK) return rc;
+    for (int k = 0; k < h->q; ++k) h->s[k] = s[k];
+    return LBMRV_OK;
+}
+
+int lbmrv_set_reference(lbmrv_t h, double rho_ref, const double* u_ref) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_reference: NULL handle");
+    double u[3] = {0.0, 0.0, 0.0};
+    for (int a = 0; a < h->dim && u_ref; ++a) u[a] = u_ref[a];
+    if (!std::isfinite(rho_ref) || !std::isfinite(u[0]) || !std::isfinite(u[1]) ||
+        !std::isfinite(u[2]))
+        return fail(h, LBMRV_E_INVAL, "lbmrv_set_reference: values must be finite");
+    h->rho_ref = rho_ref;
+    for (int a = 0; a < 3; ++a) h->u_ref[a] = u[a];
     return LBMRV_OK;
 }
 
@@ -192,6 +235,8 @@ int lbmrv_set_utilde(lbmrv_t h, const float* ut0_dev, double amplitude, double p
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_utilde: NULL handle");
     if (!std::isfinite(amplitude) || !std::isfinite(period))
         return fail(h, LBMRV_E_INVAL, "lbmrv_set_utilde: amplitude and period must be finite");
+    if (h->lattice == LBMRV_D3Q19 && h->umode == LBMRV_UT_PRESCRIBED && !ut0_dev)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_set_utilde: D3Q19 needs a u~0 field");
     h->ut0 = ut0_dev;
     h->amp = amplitude;
     h->period = period;
@@ -202,8 +247,13 @@ int lbmrv_init_equilibrium(lbmrv_t h, const float* rho_dev, const float* u_dev) 
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_init_equilibrium: NULL handle");
     if (!u_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_init_equilibrium: u is NULL");
     DeviceGuard g(h->device);
-    cudaError_t e = launch_init_eq(h->storage, h->f[h->cur], rho_dev, u_dev, h->n,
-                                   (float)h->rho_ref, (float)(1.0 / h->lambda), h->stream);
+    cudaError_t e;
+    if (h->lattice == LBMRV_D2Q9)
+        e = launch_init_eq(h->storage, h->f[h->cur], rho_dev, u_dev, h->n, store_ref(h),
+                           (float)(1.0 / h->lambda), h->stream);
+    else
+        e = launch_init_eq3(h->storage, h->f[h->cur], rho_dev, u_dev, h->n, store_ref3(h),
+                            (float)(1.0 / h->lambda), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_init_equilibrium");
     h->t = 0;
     return LBMRV_OK;
@@ -213,16 +263,21 @@ int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_init_equilibrium_host: NULL handle");
     if (!u_host) return fail(h, LBMRV_E_INVAL, "lbmrv_init_equilibrium_host: u is NULL");
     DeviceGuard g(h->device);
-    // Staging: 3 floats per node fit in the non-current state buffer (>= 18 bytes per node).
+    // Staging: 1 + d floats per node fit in the non-current state buffer (>= 18 bytes/node).
     float* stage = static_cast<float*>(h->f[1 - h->cur]);
     const size_t nb = sizeof(float) * (size_t)h->n;
     cudaError_t e = cudaSuccess;
     if (rho_host) e = cudaMemcpyAsync(stage, rho_host, nb, cudaMemcpyHostToDevice, h->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(stage + h->n, u_host, 2 * nb, cudaMemcpyHostToDevice, h->stream);
+        e = cudaMemcpyAsync(stage + h->n, u_host, h->dim * nb, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_init_equilibrium_host: copy");
-    e = launch_init_eq(h->storage, h->f[h->cur], rho_host ? stage : nullptr, stage + h->n, h->n,
-                       (float)h->rho_ref, (float)(1.0 / h->lambda), h->stream);
+    const float* rho = rho_host ? stage : nullptr;
+    if (h->lattice == LBMRV_D2Q9)
+        e = launch_init_eq(h->storage, h->f[h->cur], rho, stage + h->n, h->n, store_ref(h),
+                           (float)(1.0 / h->lambda), h->stream);
+    else
+        e = launch_init_eq3(h->storage, h->f[h->cur], rho, stage + h->n, h->n, store_ref3(h),
+                            (float)(1.0 / h->lambda), h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_init_equilibrium_host");
     h->t = 0;
     return LBMRV_OK;
@@ -231,13 +286,12 @@ int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u
 int lbmrv_step(lbmrv_t h, int64_t n) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_step: NULL handle");
     if (n < 0) return fail(h, LBMRV_E_INVAL, "lbmrv_step: n < 0");
+    if (h->lattice == LBMRV_D3Q19 && h->umode == LBMRV_UT_PRESCRIBED && !h->ut0)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_step: D3Q19 prescribed mode needs a u~0 field");
     DeviceGuard g(h->device);
-    const int um = kernel_mode(h);
     const int nv = choose_width(h, h->f[0], h->f[1]);
     for (int64_t k = 0; k < n; ++k) {
-        const StepArgs a = make_args(h, h->t + 1);
-        cudaError_t e = launch_step(h->storage, um, nv, h->f[h->cur], h->f[1 - h->cur], a,
-                                    h->stream);
+        cudaError_t e = launch_handle_step(h, nv, h->f[h->cur], h->f[1 - h->cur], h->t + 1);
         if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_step");
         h->cur = 1 - h->cur;
         h->t += 1;
@@ -245,11 +299,18 @@ int lbmrv_step(lbmrv_t h, int64_t n) {
     return LBMRV_OK;
 }
 
+static cudaError_t moments_into(lbmrv_t h, float* rho, float* u) {
+    if (h->lattice == LBMRV_D2Q9)
+        return launch_moments(h->storage, h->f[h->cur], rho, u, h->n, store_ref(h),
+                              (float)h->lambda, h->stream);
+    return launch_moments3(h->storage, h->f[h->cur], rho, u, h->n, store_ref3(h),
+                           (float)h->lambda, h->stream);
+}
+
 int lbmrv_moments(lbmrv_t h, float* rho_dev, float* u_dev) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_moments: NULL handle");
     DeviceGuard g(h->device);
-    cudaError_t e = launch_moments(h->storage, h->f[h->cur], rho_dev, u_dev, h->n,
-                                   (float)h->rho_ref, (float)h->lambda, h->stream);
+    cudaError_t e = moments_into(h, rho_dev, u_dev);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_moments");
     return LBMRV_OK;
 }
@@ -259,38 +320,66 @@ int lbmrv_moments_host(lbmrv_t h, float* rho_host, float* u_host) {
     DeviceGuard g(h->device);
     float* stage = static_cast<float*>(h->f[1 - h->cur]);
     const size_t nb = sizeof(float) * (size_t)h->n;
-    cudaError_t e = launch_moments(h->storage, h->f[h->cur], stage, stage + h->n, h->n,
-                                   (float)h->rho_ref, (float)h->lambda, h->stream);
+    cudaError_t e = moments_into(h, stage, stage + h->n);
     if (e == cudaSuccess && rho_host)
         e = cudaMemcpyAsync(rho_host, stage, nb, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess && u_host)
-        e = cudaMemcpyAsync(u_host, stage + h->n, 2 * nb, cudaMemcpyDeviceToHost, h->stream);
+        e = cudaMemcpyAsync(u_host, stage + h->n, h->dim * nb, cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_moments_host");
     return LBMRV_OK;
 }
 
+int lbmrv_conserved3(lbmrv_t h, double out_host[5]) {
+    if (!h || !out_host) return fail(h, LBMRV_E_INVAL, "lbmrv_conserved3: NULL argument");
+    DeviceGuard g(h->device);
+    double* res = h->red + 8 * (size_t)h->red_blocks;
+    cudaError_t e;
+    double tmp[5] = {0, 0, 0, 0, 0};
+    if (h->lattice == LBMRV_D2Q9) {
+        double four[4] = {0, 0, 0, 0};
+        e = launch_conserved(h->storage, h->f[h->cur], h->n, h->rho_ref,
+                             h->rho_ref * h->u_ref[0] / h->lambda,
+                             h->rho_ref * h->u_ref[1] / h->lambda, h->lambda, h->red,
+                             h->red_blocks, res, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(four, res, sizeof(four), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+        tmp[0] = four[0];
+        tmp[1] = four[1];
+        tmp[2] = four[2];
+        tmp[4] = four[3];
+    } else {
+        e = launch_conserved3(h->storage, h->f[h->cur], h->n, store_ref3(h), h->lambda, h->red,
+                              h->red_blocks, res, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp, res, sizeof(tmp), cudaMemcpyDeviceToHost, h->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_conserved");
+    for (int k = 0; k < 5; ++k) out_host[k] = tmp[k];
+    if (out_host[4] > 0.0)
+        return fail(h, LBMRV_E_NONFINITE, "lbmrv_conserved: %.0f nodes hold non-finite values",
+                    out_host[4]);
+    return LBMRV_OK;
+}
+
 int lbmrv_conserved(lbmrv_t h, double out_host[4]) {
     if (!h || !out_host) return fail(h, LBMRV_E_INVAL, "lbmrv_conserved: NULL argument");
-    DeviceGuard g(h->device);
-    double* res = h->red + 4 * (size_t)h->red_blocks;
-    cudaError_t e = launch_conserved(h->storage, h->f[h->cur], h->n, h->rho_ref, h->lambda,
-                                     h->red, h->red_blocks, res, h->stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(out_host, res, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_conserved");
-    if (out_host[3] > 0.0)
-        return fail(h, LBMRV_E_NONFINITE, "lbmrv_conserved: %.0f nodes hold non-finite values",
-                    out_host[3]);
-    return LBMRV_OK;
+    double five[5];
+    const int rc = lbmrv_conserved3(h, five);
+    if (rc != LBMRV_OK && rc != LBMRV_E_NONFINITE) return rc;
+    out_host[0] = five[0];
+    out_host[1] = five[1];
+    out_host[2] = five[2];
+    out_host[3] = five[4];
+    return rc;
 }
 
 int lbmrv_get_state(lbmrv_t h, void* dst_dev) {
     if (!h || !dst_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_get_state: NULL argument");
     DeviceGuard g(h->device);
-    const size_t bytes = (size_t)(9 * h->n * elem_size(h->storage));
-    cudaError_t e = cudaMemcpyAsync(dst_dev, h->f[h->cur], bytes, cudaMemcpyDeviceToDevice,
+    cudaError_t e = cudaMemcpyAsync(dst_dev, h->f[h->cur], state_bytes(h), cudaMemcpyDeviceToDevice,
                                     h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_get_state");
     return LBMRV_OK;
@@ -300,8 +389,7 @@ int lbmrv_set_state(lbmrv_t h, const void* src_dev, int64_t t) {
     if (!h || !src_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_set_state: NULL argument");
     if (t < 0) return fail(h, LBMRV_E_INVAL, "lbmrv_set_state: t < 0");
     DeviceGuard g(h->device);
-    const size_t bytes = (size_t)(9 * h->n * elem_size(h->storage));
-    cudaError_t e = cudaMemcpyAsync(h->f[h->cur], src_dev, bytes, cudaMemcpyDeviceToDevice,
+    cudaError_t e = cudaMemcpyAsync(h->f[h->cur], src_dev, state_bytes(h), cudaMemcpyDeviceToDevice,
                                     h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_set_state");
     h->t = t;

@@ -29,10 +29,15 @@ def storage_id(storage) -> int:
 class D2Q9:
     """A periodic nx x ny D2Q9 lattice advanced by the relative-velocity scheme."""
 
+    LATTICE = B.LBMRV_D2Q9
+    Q = 9
+    DIM = 2
+
     def __init__(self, nx: int, ny: int, s, mode="fluid", storage="fp32", lam: float = 1.0,
-                 rho_ref: float | None = None, device=None, stream=None):
-        self.nx, self.ny = int(nx), int(ny)
-        self.n = self.nx * self.ny
+                 rho_ref: float | None = None, device=None, stream=None, u_ref=None, nz: int = 1):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.n = self.nx * self.ny * self.nz
+        self.shape = (self.ny, self.nx) if self.DIM == 2 else (self.nz, self.ny, self.nx)
         self.mode = mode_id(mode)
         self.storage = storage_id(storage)
         self.lam = float(lam)
@@ -41,16 +46,20 @@ class D2Q9:
         self.rho_ref = float(rho_ref)
         self.device = torch.device(device) if device is not None else torch.device(
             "cuda", torch.cuda.current_device())
-        nbytes = B.lbmrv_state_bytes(B.LBMRV_D2Q9, (self.nx, self.ny, 1), self.storage)
+        dims = (self.nx, self.ny, self.nz)
+        nbytes = B.lbmrv_state_bytes(self.LATTICE, dims, self.storage)
         if nbytes <= 0:
-            raise ValueError(f"invalid lattice {nx} x {ny}")
+            raise ValueError(f"invalid lattice {dims}")
         self._bufs = [torch.empty(nbytes, dtype=torch.uint8, device=self.device)
                       for _ in range(2)]
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         with torch.cuda.device(self.device):
-            self.h = B.lbmrv_create(B.LBMRV_D2Q9, (self.nx, self.ny, 1), self.lam, list(s),
-                                    self.mode, self.storage, self.rho_ref, self.stream,
+            self.h = B.lbmrv_create(self.LATTICE, dims, self.lam, list(s), self.mode,
+                                    self.storage, self.rho_ref, self.stream,
                                     self._bufs[0], self._bufs[1])
+        self.u_ref = tuple(float(v) for v in (u_ref or (0.0,) * self.DIM))
+        if any(v != 0.0 for v in self.u_ref):
+            B.lbmrv_set_reference(self.h, self.rho_ref, self.u_ref)
         self._ut0 = None
         self.s = [float(v) for v in s]
         self.amp, self.period = 0.0, 0.0
@@ -86,17 +95,19 @@ class D2Q9:
         self.amp, self.period = float(amplitude), float(period)
         if ut0 is not None:
             ut0 = torch.as_tensor(ut0, dtype=torch.float32, device=self.device).contiguous()
-            if ut0.numel() != 2 * self.n:
-                raise ValueError("u~0 must hold 2 * nx * ny values")
+            if ut0.numel() != self.DIM * self.n:
+                raise ValueError(f"u~0 must hold {self.DIM} * n values")
         self._ut0 = ut0  # keep the field alive while the handle refers to it
         B.lbmrv_set_utilde(self.h, ut0, amplitude, period)
 
     # -- state
-    def init_equilibrium(self, rho, ux, uy):
+    def init_equilibrium(self, rho, *u_components):
+        """rho and the d velocity components, each shaped like the lattice."""
+        if len(u_components) != self.DIM:
+            raise ValueError(f"expected {self.DIM} velocity components")
         rho = torch.as_tensor(rho, dtype=torch.float32, device=self.device).contiguous()
-        u = torch.stack([torch.as_tensor(ux, dtype=torch.float32, device=self.device),
-                         torch.as_tensor(uy, dtype=torch.float32, device=self.device)])
-        u = u.contiguous()
+        u = torch.stack([torch.as_tensor(c, dtype=torch.float32, device=self.device)
+                         for c in u_components]).contiguous()
         B.lbmrv_init_equilibrium(self.h, rho, u)
         self._keep = (rho, u)  # the copy is asynchronous on the stream
 
@@ -112,32 +123,40 @@ class D2Q9:
         return B.lbmrv_time(self.h)
 
     def moments(self):
-        rho = torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device)
-        u = torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
+        """rho and the d velocity components (device tensors shaped like the lattice)."""
+        rho = torch.empty(self.shape, dtype=torch.float32, device=self.device)
+        u = torch.empty((self.DIM,) + self.shape, dtype=torch.float32, device=self.device)
         B.lbmrv_moments(self.h, rho, u)
-        return rho, u[0], u[1]
+        return (rho,) + tuple(u[a] for a in range(self.DIM))
 
     def moments_host(self, rho_host=None, u_host=None):
         if rho_host is None:
-            rho_host = torch.empty((self.ny, self.nx), dtype=torch.float32, pin_memory=True)
+            rho_host = torch.empty(self.shape, dtype=torch.float32, pin_memory=True)
         if u_host is None:
-            u_host = torch.empty((2, self.ny, self.nx), dtype=torch.float32, pin_memory=True)
+            u_host = torch.empty((self.DIM,) + self.shape, dtype=torch.float32,
+                                 pin_memory=True)
         B.lbmrv_moments_host(self.h, rho_host, u_host)
         return rho_host, u_host
 
     def conserved(self, allow_nonfinite: bool = False):
+        """[sum rho, sum q_x, sum q_y, non-finite nodes] (D2Q9 layout)."""
         return B.lbmrv_conserved(self.h, allow_nonfinite=allow_nonfinite)
 
+    def conserved3(self, allow_nonfinite: bool = False):
+        """[sum rho, sum q_x, sum q_y, sum q_z, non-finite nodes]."""
+        return B.lbmrv_conserved3(self.h, allow_nonfinite=allow_nonfinite)
+
     def state(self) -> torch.Tensor:
-        """Copy of the stored state g = f - w rho_ref, shape (9, ny, nx), storage dtype."""
-        out = torch.empty((9, self.ny, self.nx), dtype=self.dtype, device=self.device)
+        """Copy of the stored state g = f - f_eq(rho_ref, u_ref), shape (9, ny, nx), in the
+        storage dtype."""
+        out = torch.empty((self.Q,) + self.shape, dtype=self.dtype, device=self.device)
         B.lbmrv_get_state(self.h, out)
         return out
 
     def set_state(self, g: torch.Tensor, t: int = 0):
         g = g.to(device=self.device, dtype=self.dtype).contiguous()
-        if g.numel() != 9 * self.n:
-            raise ValueError("state must hold 9 * nx * ny values")
+        if g.numel() != self.Q * self.n:
+            raise ValueError(f"state must hold {self.Q} * n values")
         B.lbmrv_set_state(self.h, g, t)
         self._keep = g
 
@@ -187,3 +206,15 @@ class D2Q9:
         B.lbmrv_equilibrium_vjp(self.h, None if rho is None else rho.contiguous(),
                                 u.contiguous(), dL_dS0.contiguous(), drho, du)
         return drho, du
+
+
+class D3Q19(D2Q9):
+    """A periodic nx x ny x nz D3Q19 lattice advanced by the relative-velocity scheme
+    (19 rates in the order of the 3D basis of include/lbmrv.h). No adjoint."""
+
+    LATTICE = B.LBMRV_D3Q19
+    Q = 19
+    DIM = 3
+
+    def __init__(self, nx: int, ny: int, nz: int, s, **kw):
+        super().__init__(nx, ny, s, nz=nz, **kw)

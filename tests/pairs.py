@@ -15,14 +15,23 @@ def f32_fields(d):
     return tuple(inp.to_f32_exact(d[k]) for k in ("rho", "ux", "uy"))
 
 
+def reference_populations(rho_ref, u_ref, lam=1.0):
+    """Textbook D2Q9 equilibrium of the reference state (the stored offset)."""
+    cx = np.array([0, 1, 0, -1, 0, 1, -1, -1, 1], float)
+    cy = np.array([0, 0, 1, 0, -1, 1, 1, -1, -1], float)
+    ux, uy = u_ref[0] / lam, u_ref[1] / lam
+    cu = cx * ux + cy * uy
+    return W * rho_ref * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
+
+
 def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=None,
-            ut0=None, amp=0.0, period=0.0, width=0):
+            ut0=None, amp=0.0, period=0.0, width=0, u_ref=(0.0, 0.0)):
     import torch
 
     from paper_1312_3297_gb300 import D2Q9
 
     rho, ux, uy = fields
-    sim = D2Q9(nx, ny, s, mode=mode, storage=storage, lam=lam, rho_ref=rho_ref)
+    sim = D2Q9(nx, ny, s, mode=mode, storage=storage, lam=lam, rho_ref=rho_ref, u_ref=u_ref)
     if width:
         sim.set_kernel_width(width)
     if MODES[mode] == 2:
@@ -31,7 +40,7 @@ def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=Non
     sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
     sim.step(steps)
     g = sim.state().double().cpu().numpy()
-    f = g + W[:, None, None] * sim.rho_ref
+    f = g + reference_populations(sim.rho_ref, u_ref, lam)[:, None, None]
     r, a, b = (t.double().cpu().numpy() for t in sim.moments())
     sim.close()
     return f, (r, a, b)
@@ -75,7 +84,7 @@ def oracle_kinetic_energy(rho0, u0, s, mode, steps, amp=0.0, period=0.0, ut0=Non
 
 
 def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=None,
-                  field_grad=False):
+                  field_grad=False, u_ref=(0.0, 0.0)):
     """Kinetic energy after `steps` steps and its gradients from the CUDA adjoint:
     (L, dL/du0 [2, ny, nx], dL/ds [9], dL/dA, dL/du~0 or None)."""
     import torch
@@ -83,7 +92,7 @@ def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=
     from paper_1312_3297_gb300 import D2Q9
 
     rho, ux, uy = fields
-    sim = D2Q9(nx, ny, s, mode=mode)
+    sim = D2Q9(nx, ny, s, mode=mode, u_ref=u_ref)
     if MODES[mode] == 2:
         sim.set_utilde(None if ut0 is None else torch.as_tensor(ut0, dtype=torch.float32),
                        amp, period)
@@ -99,3 +108,57 @@ def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=
            None if dut is None else dut.double().cpu().numpy())
     sim.close()
     return out
+
+
+# ------------------------------------------------------------------ D3Q19
+S3 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
+W3 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+C3 = np.array([[0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0],
+               [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1],
+               [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]], float)
+
+
+def reference_populations3(rho_ref, u_ref):
+    cu = C3.T @ np.asarray(u_ref, float)
+    return W3 * rho_ref * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * float(np.dot(u_ref, u_ref)))
+
+
+def gpu_run3(shape, s, mode, steps, rho, u, storage="fp32", ut0=None, amp=0.0, period=0.0,
+             width=0, u_ref=None):
+    """shape = (nx, ny, nz); rho (nz, ny, nx), u (3, nz, ny, nx). Returns (f, rho, u)."""
+    import torch
+
+    from paper_1312_3297_gb300 import D3Q19
+
+    nx, ny, nz = shape
+    sim = D3Q19(nx, ny, nz, s, mode=mode, storage=storage, u_ref=u_ref)
+    if width:
+        sim.set_kernel_width(width)
+    if MODES[mode] == 2:
+        sim.set_utilde(torch.as_tensor(ut0, dtype=torch.float32), amp, period)
+    sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in u))
+    sim.step(steps)
+    g = sim.state().double().cpu().numpy()
+    f = g + reference_populations3(sim.rho_ref, u_ref or (0, 0, 0))[:, None, None, None]
+    m = [t.double().cpu().numpy() for t in sim.moments()]
+    sim.close()
+    return f, m[0], np.stack(m[1:])
+
+
+def oracle_run3(s, mode, steps, rho, u, ut0=None, amp=0.0, period=0.0, nthreads=8):
+    from oracle import d3q19 as o3
+
+    f0 = o3.init_equilibrium(rho, u, 1.0)
+    ut = None if ut0 is None else inp.to_f32_exact(ut0)
+    S = o3.post_collision_state(f0, 1.0, np.asarray(s, float), MODES[mode], steps, ut0=ut,
+                                amp=amp, period=period, nthreads=nthreads)
+    r, uu = o3.moments(S, 1.0)
+    return S, r, uu
+
+
+def rel_errors3(f_g, r_g, u_g, f_o, r_o, u_o):
+    e_rho = np.abs(r_g - r_o).max() / np.abs(r_o).max()
+    du = np.sqrt(((u_g - u_o) ** 2).sum(0)).max()
+    e_u = du / max(np.sqrt((u_o ** 2).sum(0)).max(), 1e-300)
+    e_f = np.abs(f_g - f_o).max() / np.abs(f_o).max()
+    return e_rho, e_u, e_f

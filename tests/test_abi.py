@@ -49,6 +49,8 @@ def test_version_and_state_bytes():
     assert B.lbmrv_state_bytes(B.LBMRV_D2Q9, (0, 5, 1), B.LBMRV_FP32) == -1
     assert B.lbmrv_state_bytes(B.LBMRV_D2Q9, (4, 5, 1), 7) == -1
     assert B.lbmrv_state_bytes(5, (4, 5, 1), 0) == -1
+    assert B.lbmrv_state_bytes(B.LBMRV_D3Q19, (4, 5, 6), B.LBMRV_FP32) == 19 * 120 * 4
+    assert B.lbmrv_state_bytes(B.LBMRV_D3Q19, (4, 5, 0), B.LBMRV_FP32) == -1
 
 
 S_OK = [0, 0, 0, 1.4, 1.9, 1.9, 1.2, 1.2, 1.4]
@@ -65,7 +67,7 @@ S_OK = [0, 0, 0, 1.4, 1.9, 1.9, 1.2, 1.2, 1.4]
     (dict(lam=float("inf")), -1, "lambda"),
     (dict(umode=3), -1, "mode"),
     (dict(storage=9), -1, "storage"),
-    (dict(lattice=1), -6, "D3Q19"),
+    (dict(lattice=1), -1, "s[3]"),
     (dict(lattice=4), -1, "lattice"),
     (dict(rho_ref=float("nan")), -1, "rho_ref"),
 ])

@@ -165,3 +165,14 @@ def test_adjoint_full_size_1024_2000_steps():
     base = np.stack([np.cos(2 * np.pi * np.arange(n)[:, None] / n) * np.ones((1, n)),
                      np.sin(2 * np.pi * np.arange(n)[None, :] / n) * np.ones((n, 1))])
     np.testing.assert_allclose(0.03 * a[3], (base * a[4]).sum(), rtol=1e-4)
+
+
+def test_adjoint_with_reference_velocity_storage():
+    """A reference velocity in the stored state changes no gradient."""
+    nx, ny, steps = 48, 40, 30
+    fields = f32_fields(inp.noisy_shear_wave(nx, ny, seed=8))
+    a = gpu_gradients(nx, ny, S, "fluid", steps, 6, fields)
+    b = gpu_gradients(nx, ny, S, "fluid", steps, 6, fields, u_ref=(0.04, -0.01))
+    assert abs(a[0] - b[0]) <= 1e-6 * abs(a[0])
+    assert _rel(b[1], a[1]) <= 1e-4
+    assert abs(b[2][4] + b[2][5] - a[2][4] - a[2][5]) <= 1e-4 * abs(a[2][4] + a[2][5])

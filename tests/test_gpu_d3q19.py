@@ -1,0 +1,110 @@
+"""GPU parity of the fused D3Q19 relative-velocity step against the FP64 D3Q19 oracle."""
+import os
+
+import numpy as np
+import pytest
+
+import lbm_inputs as inp
+from pairs import S3, W3, gpu_run3, oracle_run3, reference_populations3, rel_errors3
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _fields(shape, seed):
+    nx, ny, nz = shape
+    d = inp.random_flow_3d(nx, ny, nz, seed=seed)
+    return inp.to_f32_exact(d["rho"]), inp.to_f32_exact(d["u"])
+
+
+def _check(shape, mode, steps, tol=TOL, seed=0, **kw):
+    rho, u = _fields(shape, seed)
+    nx, ny, nz = shape
+    ut0 = None
+    if mode == "prescribed":
+        ut0 = inp.to_f32_exact(np.random.default_rng(seed + 7).standard_normal((3, nz, ny, nx)))
+    f_g, r_g, u_g = gpu_run3(shape, S3, mode, steps, rho, u, ut0=ut0, amp=0.03, period=40.0,
+                             **kw)
+    f_o, r_o, u_o = oracle_run3(S3, mode, steps, rho, u, ut0=ut0, amp=0.03, period=40.0)
+    e = rel_errors3(f_g, r_g, u_g, f_o, r_o, u_o)
+    assert max(e) <= tol, (shape, mode, kw, e)
+    return f_g
+
+
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed"])
+def test_parity_small_3d_every_width(mode):
+    shape = (24, 10, 8)
+    outs = [_check(shape, mode, 20, width=w) for w in (1, 2, 4)]
+    for f in outs[1:]:
+        np.testing.assert_array_equal(f, outs[0])
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (7, 3, 2), (2, 9, 1), (5, 1, 4)])
+def test_parity_degenerate_3d(shape):
+    for mode in ("zero", "fluid", "prescribed"):
+        _check(shape, mode, 6)
+
+
+def test_parity_3d_reference_velocity():
+    _check((16, 12, 6), "fluid", 25, u_ref=(0.03, -0.02, 0.01))
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_reduced_precision_3d(storage):
+    shape = (32, 16, 12)
+    rho, u = _fields(shape, 3)
+    f_g, r_g, u_g = gpu_run3(shape, S3, "fluid", 40, rho, u, storage=storage)
+    f_o, r_o, u_o = oracle_run3(S3, "fluid", 40, rho, u)
+    e = rel_errors3(f_g, r_g, u_g, f_o, r_o, u_o)
+    assert e[1] <= (2e-3 if storage == "fp16" else 2e-2), e
+
+
+def test_full_size_256_sampled_parity_and_conservation():
+    """3D Taylor-Green vortex u0 = 0.04 on 256^3 (u~ = q/rho, s_nu = 1.7) in the benchmark's
+    launch configuration: sampled nodes against the oracle on their dependency cone, and
+    mass / momentum over 100 steps."""
+    import torch
+
+    from oracle import d3q19 as o3
+    from paper_1312_3297_gb300 import D3Q19
+
+    L, steps = 256, 4
+    d = inp.taylor_green_3d(L, L, L, u0=0.04)
+    rho, u = inp.to_f32_exact(d["rho"]), inp.to_f32_exact(d["u"])
+    sim = D3Q19(L, L, L, S3, mode="fluid")
+    sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in u))
+    c0 = sim.conserved3()
+    sim.step(steps)
+    g = sim.state()
+    fref = reference_populations3(sim.rho_ref, (0, 0, 0))
+    rng = np.random.default_rng(1)
+    centers = [(0, 0, 0), (L - 1, L - 1, L - 1), (1, 0, L - 1), (127, 128, 5)]
+    centers += [tuple(int(v) for v in rng.integers(0, L, 3)) for _ in range(4)]
+    R = steps + 1
+    errs, fmax = [], 0.0
+    for cx, cy, cz in centers:
+        xs = (cx + np.arange(-R, R + 1)) % L
+        ys = (cy + np.arange(-R, R + 1)) % L
+        zs = (cz + np.arange(-R, R + 1)) % L
+        sub_rho = rho[np.ix_(zs, ys, xs)]
+        sub_u = u[:, zs][:, :, ys][:, :, :, xs]
+        f0 = o3.init_equilibrium(sub_rho, sub_u, 1.0)
+        S = o3.post_collision_state(f0, 1.0, np.array(S3, float), 1, steps, nthreads=8)
+        ref = S[:, R, R, R]
+        got = g[:, cz, cy, cx].double().cpu().numpy() + fref
+        errs.append(np.abs(got - ref).max())
+        fmax = max(fmax, np.abs(ref).max())
+    assert max(errs) / fmax <= TOL, errs
+    sim.step(96)
+    c1 = sim.conserved3()
+    assert abs(c1[0] - c0[0]) / c0[0] < 1e-9
+    for a in (1, 2, 3):
+        assert abs(c1[a] - c0[a]) < 1e-6 * c0[0] * 0.04
+    sim.close()
