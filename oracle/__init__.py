@@ -40,6 +40,8 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liblbmrv_oracle.so")
 METHOD_DEFINITION = 0
 METHOD_SHIFTED = 1
 METHOD_MRT = 2
+METHOD_GEIER = 3       # definition in Geier's basis, product (Maxwellian-moment) equilibrium
+METHOD_CASCADED = 4    # Geier's cascade as written in Appendix B (u~ = q/rho)
 MODE_ZERO = 0
 MODE_FLUID = 1
 MODE_PRESCRIBED = 2
@@ -117,6 +119,15 @@ def lib() -> ctypes.CDLL:
             L.orc_init_equilibrium.argtypes = [I64, I64, D, P, P, P, P]
             L.orc_moments.argtypes = [I64, I64, D, P, P, P, P]
             L.orc_velocities.argtypes = [D, P, P]
+            L.orc_poly_geier.restype = D
+            L.orc_poly_geier.argtypes = [I, D, D, D]
+            L.orc_moment_matrix_geier.argtypes = [D, D, D, P]
+            L.orc_feq_product.argtypes = [D, D, D, D, P]
+            L.orc_collide_geier.restype = I
+            L.orc_collide_geier.argtypes = [P, D, D, D, P, P]
+            L.orc_collide_cascaded.restype = I
+            L.orc_collide_cascaded.argtypes = [P, D, P, P]
+            L.orc_init_equilibrium_product.argtypes = [I64, I64, D, P, P, P, P]
             _lib = L
     return _lib
 
@@ -173,9 +184,35 @@ def collide_node(method: int, f, utx: float, uty: float, lam: float, s) -> np.nd
             raise FloatingPointError("singular shifted moment matrix")
     elif method == METHOD_SHIFTED:
         lib().orc_collide_shifted(_ptr(f), utx, uty, lam, _ptr(s), _ptr(out))
-    else:
+    elif method == METHOD_MRT:
         lib().orc_collide_mrt(_ptr(f), lam, _ptr(s), _ptr(out))
+    elif method == METHOD_GEIER:
+        if lib().orc_collide_geier(_ptr(f), utx, uty, lam, _ptr(s), _ptr(out)) != 0:
+            raise FloatingPointError("singular shifted moment matrix")
+    else:
+        if lib().orc_collide_cascaded(_ptr(f), lam, _ptr(s), _ptr(out)) != 0:
+            raise FloatingPointError("singular cascade")
     return out
+
+
+def moment_matrix_geier(utx: float, uty: float, lam: float) -> np.ndarray:
+    M = np.zeros((9, 9))
+    lib().orc_moment_matrix_geier(utx, uty, lam, _ptr(M))
+    return M
+
+
+def feq_product(rho: float, ux: float, uy: float, lam: float) -> np.ndarray:
+    out = np.zeros(9)
+    lib().orc_feq_product(rho, ux, uy, lam, _ptr(out))
+    return out
+
+
+def init_equilibrium_product(rho, ux, uy, lam: float) -> np.ndarray:
+    rho, ux, uy = _f64(rho), _f64(ux), _f64(uy)
+    ny, nx = rho.shape
+    f = np.zeros((9, ny, nx))
+    lib().orc_init_equilibrium_product(nx, ny, lam, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(f))
+    return f
 
 
 # ---------------------------------------------------------------- lattice level

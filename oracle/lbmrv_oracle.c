@@ -307,6 +307,10 @@ void orc_collide_mrt(const double* f, double l, const double* s, double* fstar) 
     }
 }
 
+int orc_collide_geier(const double* f, double utx, double uty, double l, const double* s,
+                      double* fstar);
+int orc_collide_cascaded(const double* f, double l, const double* s, double* fstar);
+
 /* Relative velocity at node (x, y) and collision time t.
  * mode 0: u~ = 0 (d'Humieres); 1: u~ = q/rho (cascaded-like); 2: prescribed field
  * u~ = amp * u0(x) * cos(2 pi t / period) (no time factor when period <= 0), with
@@ -338,8 +342,10 @@ static void relative_velocity(int mode, const double* f, double l, int64_t nx, i
     }
 }
 
-/* Relaxation at every node at time t (no transport). method: 0 definition,
- * 1 shifted, 2 mrt (mrt ignores the mode). Returns 0, or -1 on a singular matrix. */
+/* Relaxation at every node at time t (no transport). method: 0 definition, 1 shifted,
+ * 2 mrt (ignores the mode), 3 definition in the Geier basis with the product equilibrium,
+ * 4 Geier's cascade of Appendix B (u~ = q/rho, ignores the mode). Returns 0, or -1 on a
+ * singular matrix. */
 int orc_collide_lattice(int method, int64_t nx, int64_t ny, double l, const double* s,
                         int mode, const double* ut0, double amp, double period, int64_t t,
                         const double* fin, double* fout, int nthreads) {
@@ -357,8 +363,12 @@ int orc_collide_lattice(int method, int64_t nx, int64_t ny, double l, const doub
                 if (orc_collide_definition(f, utx, uty, l, s, fs) != 0) status = -1;
             } else if (method == 1) {
                 orc_collide_shifted(f, utx, uty, l, s, fs);
-            } else {
+            } else if (method == 2) {
                 orc_collide_mrt(f, l, s, fs);
+            } else if (method == 3) {
+                if (orc_collide_geier(f, utx, uty, l, s, fs) != 0) status = -1;
+            } else {
+                if (orc_collide_cascaded(f, l, s, fs) != 0) status = -1;
             }
             for (int j = 0; j < Q; ++j) fout[j * n + i] = fs[j];
         }
@@ -419,5 +429,169 @@ void orc_moments(int64_t nx, int64_t ny, double l, const double* f, double* rho,
         rho[i] = r;
         ux[i] = a / r;
         uy[i] = b / r;
+    }
+}
+
+/* ------------------------------------------------------------------------------------
+ * Geier's cascaded scheme as a scheme with relative velocities (proposition of Section
+ * 1.3 on the cascaded scheme, Appendix B).
+ *
+ * Basis (relation (polgeier)): 1, X, Y, X^2+Y^2, X^2-Y^2, XY, XY^2, X^2Y, X^2Y^2, divided by
+ * lambda^degree from degree 2 on. Equilibrium (reading: the paper says Geier's equilibria
+ * come from the Maxwellian but does not print them): the populations whose moments in this
+ * basis, shifted by the fluid velocity u = q/rho, are those of the Maxwellian,
+ * (rho, 0, 0, 2 rho c^2, 0, 0, 0, 0, rho c^4) with c^2 = lambda^2/3. On the D2Q9 velocities
+ * this is the product form f_eq(v) = rho phi(v_x, u_x) phi(v_y, u_y) with
+ * phi(0, a) = 2/3 - a^2/lambda^2, phi(+-lambda, a) = (1/3 + a^2/lambda^2 +- a/lambda)/2.
+ */
+double orc_poly_geier(int k, double X, double Y, double l) {
+    double l2 = l * l, l3 = l2 * l, l4 = l2 * l2;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return X;
+        case 2: return Y;
+        case 3: return (X * X + Y * Y) / l2;
+        case 4: return (X * X - Y * Y) / l2;
+        case 5: return X * Y / l2;
+        case 6: return X * Y * Y / l3;
+        case 7: return X * X * Y / l3;
+        case 8: return X * X * Y * Y / l4;
+        default: return NAN;
+    }
+}
+
+void orc_moment_matrix_geier(double ux, double uy, double l, double* M) {
+    for (int k = 0; k < Q; ++k)
+        for (int j = 0; j < Q; ++j)
+            M[k * Q + j] = orc_poly_geier(k, l * CX[j] - ux, l * CY[j] - uy, l);
+}
+
+static double phi1(int c, double a) {
+    if (c == 0) return 2.0 / 3.0 - a * a;
+    return 0.5 * (1.0 / 3.0 + a * a + c * a);
+}
+
+void orc_feq_product(double rho, double ux, double uy, double l, double* feq) {
+    for (int j = 0; j < Q; ++j) feq[j] = rho * phi1(CX[j], ux / l) * phi1(CY[j], uy / l);
+}
+
+/* Relaxation of Section 1.2 in the Geier basis with the product equilibrium. */
+int orc_collide_geier(const double* f, double utx, double uty, double l, const double* s,
+                      double* fstar) {
+    double M[Q * Q], feq[Q], m[Q], meq[Q], ms[Q];
+    double rho, qx, qy;
+    conserved(f, l, &rho, &qx, &qy);
+    orc_feq_product(rho, qx / rho, qy / rho, l, feq);
+    orc_moment_matrix_geier(utx, uty, l, M);
+    for (int k = 0; k < Q; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < Q; ++j) {
+            a += M[k * Q + j] * f[j];
+            b += M[k * Q + j] * feq[j];
+        }
+        m[k] = a;
+        meq[k] = b;
+    }
+    for (int k = 0; k < Q; ++k) ms[k] = m[k] + s[k] * (meq[k] - m[k]);
+    return orc_lu_solve(M, ms, fstar);
+}
+
+/* Geier's cascaded relaxation written as in Appendix B, coded separately from the above:
+ * moments m_g(u) in Geier's original set 1, X, Y, X^2, Y^2, XY, XY^2, X^2Y, X^2Y^2 shifted
+ * by u = q/rho; the collision f* = f + M(0)^T g (relation (relgeier), M(0) of relation
+ * (matort)) with g from C(u) g = Lambda (m_eq - m), C(u) = M_g(u) M(0)^T, solved in the
+ * cascade order: the 2x2 system on the second-order diagonal moments (relation (casc1)),
+ * the other components one after the other (relation (casc2)). Lambda is diagonal except
+ * for the block [[s+, s-], [s-, s+]] on (X^2, Y^2), s+- = (s3 +- s4)/2, where s3 and s4 are
+ * the rates of X^2+Y^2 and X^2-Y^2 (s given in the order of orc_collide_geier). */
+int orc_collide_cascaded(const double* f, double l, const double* s, double* fstar) {
+    static const int MI[Q][Q] = {
+        { 1,  1,  1,  1,  1,  1,  1,  1,  1},
+        { 0,  1,  0, -1,  0,  1, -1, -1,  1},
+        { 0,  0,  1,  0, -1,  1,  1, -1, -1},
+        {-4, -1, -1, -1, -1,  2,  2,  2,  2},
+        { 0,  1, -1,  1, -1,  0,  0,  0,  0},
+        { 0,  0,  0,  0,  0,  1, -1,  1, -1},
+        { 0, -2,  0,  2,  0,  1, -1, -1,  1},
+        { 0,  0, -2,  0,  2,  1,  1, -1, -1},
+        { 4, -2, -2, -2, -2,  1,  1,  1,  1}};
+    double rho = 0.0, qx = 0.0, qy = 0.0;
+    for (int j = 0; j < Q; ++j) {
+        rho += f[j];
+        qx += l * CX[j] * f[j];
+        qy += l * CY[j] * f[j];
+    }
+    const double ux = qx / rho, uy = qy / rho;
+    double feq[Q];
+    orc_feq_product(rho, ux, uy, l, feq);
+    /* Geier's original moments shifted by u */
+    double Mg[Q][Q], m[Q], meq[Q];
+    for (int j = 0; j < Q; ++j) {
+        const double X = l * CX[j] - ux, Y = l * CY[j] - uy;
+        const double l2 = l * l, l3 = l2 * l, l4 = l2 * l2;
+        const double p[Q] = {1.0, X, Y, X * X / l2, Y * Y / l2, X * Y / l2, X * Y * Y / l3,
+                             X * X * Y / l3, X * X * Y * Y / l4};
+        for (int k = 0; k < Q; ++k) Mg[k][j] = p[k];
+    }
+    for (int k = 0; k < Q; ++k) {
+        double a = 0.0, b = 0.0;
+        for (int j = 0; j < Q; ++j) {
+            a += Mg[k][j] * f[j];
+            b += Mg[k][j] * feq[j];
+        }
+        m[k] = a;
+        meq[k] = b;
+    }
+    /* right-hand side Lambda (m_eq - m) */
+    const double sp = 0.5 * (s[3] + s[4]), sm = 0.5 * (s[3] - s[4]);
+    double rhs[Q];
+    for (int k = 0; k < Q; ++k) rhs[k] = 0.0;
+    rhs[3] = sp * (meq[3] - m[3]) + sm * (meq[4] - m[4]);
+    rhs[4] = sm * (meq[3] - m[3]) + sp * (meq[4] - m[4]);
+    for (int k = 5; k < Q; ++k) rhs[k] = s[k] * (meq[k] - m[k]);
+    /* C(u) = M_g(u) M(0)^T (rows of M(0) with lambda on rows 1, 2) */
+    double C[Q][Q];
+    for (int k = 0; k < Q; ++k)
+        for (int c = 0; c < Q; ++c) {
+            double a = 0.0;
+            const double scale = (c == 1 || c == 2) ? l : 1.0;
+            for (int j = 0; j < Q; ++j) a += Mg[k][j] * scale * MI[c][j];
+            C[k][c] = a;
+        }
+    /* cascade: g_0 = g_1 = g_2 = 0 (conserved moments do not change); then the 2x2 block of
+     * rows 3, 4 in the unknowns g_3, g_4; then rows 5..8, each solved for g_k using the
+     * components already known. The system is lower triangular apart from that block. */
+    double g[Q] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    {
+        const double a = C[3][3], b = C[3][4], c = C[4][3], d = C[4][4];
+        const double det = a * d - b * c;
+        if (det == 0.0) return -1;
+        g[3] = (d * rhs[3] - b * rhs[4]) / det;
+        g[4] = (a * rhs[4] - c * rhs[3]) / det;
+    }
+    for (int k = 5; k < Q; ++k) {
+        double acc = rhs[k];
+        for (int c = 3; c < k; ++c) acc -= C[k][c] * g[c];
+        if (C[k][k] == 0.0) return -1;
+        g[k] = acc / C[k][k];
+    }
+    for (int j = 0; j < Q; ++j) {
+        double a = 0.0;
+        for (int c = 0; c < Q; ++c) {
+            const double scale = (c == 1 || c == 2) ? l : 1.0;
+            a += scale * MI[c][j] * g[c];
+        }
+        fstar[j] = f[j] + a;
+    }
+    return 0;
+}
+
+void orc_init_equilibrium_product(int64_t nx, int64_t ny, double l, const double* rho,
+                                  const double* ux, const double* uy, double* f) {
+    int64_t n = nx * ny;
+    for (int64_t i = 0; i < n; ++i) {
+        double feq[Q];
+        orc_feq_product(rho[i], ux[i], uy[i], l, feq);
+        for (int j = 0; j < Q; ++j) f[j * n + i] = feq[j];
     }
 }
