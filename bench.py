@@ -151,6 +151,33 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(value: float, device) -> float:
+    """The slowest rank's value: an all-reduce MAX over the default process group (the
+    value itself when no group is initialised or it has one rank)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes_per_rank: int, world: int, steps: int, ms_max: float) -> float:
+    """Whole-job throughput of `world` replicas, each advancing `nodes_per_rank` nodes by
+    `steps` steps, timed by the slowest rank (weak scaling)."""
+    return world * nodes_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
+def default_width(lattice: str, storage: str, nx: int) -> int:
+    """Nodes per thread of the automatically chosen step kernel (the library's rule)."""
+    widest = (4 if storage == "fp32" else 8) if lattice == "d2q9" else (4 if storage == "fp32" else 2)
+    while widest > 1 and nx % widest:
+        widest //= 2
+    return widest
+
+
 # ------------------------------------------------------------------ GPU arm
 def time_steps(sim, steps: int, torch):
     """Device time (ms) of `steps` fused steps on the handle's stream, CUDA events."""
@@ -200,9 +227,20 @@ def gpu_arm(args):
     binding.load()
     peak, peak_kind = measured_peaks()
     size = args.size
-    n = size * size
-    fields = inp.taylor_green(size, size, u0=0.04)
-    sim = make_sim(torch, D2Q9, inp, args.storage, args.mode, size, fields)
+    if args.lattice == "d3q19":
+        from paper_1312_3297_gb300 import D3Q19
+
+        n = size ** 3
+        d3 = inp.taylor_green_3d(size, size, size, u0=0.04)
+        sim = D3Q19(size, size, size, [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3,
+                    mode="fluid" if args.mode == "prescribed" else args.mode, storage=args.storage)
+        sim.init_equilibrium(torch.as_tensor(d3["rho"], dtype=torch.float32),
+                             *(torch.as_tensor(c, dtype=torch.float32) for c in d3["u"]))
+        del d3
+    else:
+        n = size * size
+        fields = inp.taylor_green(size, size, u0=0.04)
+        sim = make_sim(torch, D2Q9, inp, args.storage, args.mode, size, fields)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
@@ -222,16 +260,15 @@ def gpu_arm(args):
         last = clocks.mark()
         clocks.stop()
         clock_info = clocks.summary(first, last)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, torch.device("cuda", local))
     finite = sim.conserved(allow_nonfinite=True)
     sim.close()
     per_step_ms = ms / args.steps
-    mlups = world * n * args.steps / (ms * 1e-3) / 1e6
-    achieved = BYTES_PER_NODE[args.storage] * n / (per_step_ms * 1e-3) / 1e9
-    headline = size == L and args.storage == "fp32" and args.mode == "prescribed"
+    mlups = job_mlups(n, world, args.steps, ms)
+    bpn = BYTES_PER_NODE[args.storage] * (19 / 9 if args.lattice == "d3q19" else 1)
+    achieved = bpn * n / (per_step_ms * 1e-3) / 1e9
+    headline = (size == L and args.storage == "fp32" and args.mode == "prescribed"
+                and args.lattice == "d2q9")
     out = None
     if rank == 0:
         extras = {}
@@ -252,6 +289,7 @@ def gpu_arm(args):
             extras["fp32_fluid_8192"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", 8192,
                                                      big, k, peak)
             del big
+            extras["cascaded_geier_fluid"] = cascaded_measure(torch, inp, fields, k, peak)
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
             extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
         e2e = (e2e_measure(torch, D2Q9, inp, fields, args.steps)
@@ -264,15 +302,17 @@ def gpu_arm(args):
             "dtype": "f32" if args.storage == "fp32" else f"{args.storage} storage, f32 math",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if headline else
-                       f"D2Q9 {args.storage} {size}x{size} Taylor-Green, u~ mode {args.mode}",
-                       "nodes": n, "bytes_per_node_step": BYTES_PER_NODE[args.storage],
+                       f"{args.lattice} {args.storage} side {size} Taylor-Green, u~ mode {args.mode}",
+                       "nodes": n, "bytes_per_node_step": round(bpn, 1),
                        "l2": "state 1.2 GB > 129 MB L2; no flush needed",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": recorded_traffic() if headline else None,
                          "peak_kind": peak_kind,
-                         "kernel": f"k_step_vec<{args.storage},4,{args.mode}>"},
+                         "kernel": (f"{'k_step_vec' if args.lattice == 'd2q9' else 'k_step3'}"
+                                    f"<{args.storage},{default_width(args.lattice, args.storage, size)},"
+                                    f"{args.mode}>")},
             "clocks": clock_info,
             "e2e": e2e,
             "gpu_launches": args.steps,
@@ -286,6 +326,23 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def cascaded_measure(torch, inp, fields, steps, peak):
+    """Geier's cascaded scheme (D2Q9, Geier basis, product equilibrium, u~ = q/rho) on the
+    same 4096^2 Taylor-Green workload, FP32."""
+    from paper_1312_3297_gb300 import D2Q9Cascaded
+
+    sim = D2Q9Cascaded(L, L, [0, 0, 0, 1.3, 1.8, 1.8, 1.5, 1.5, 1.2], mode="fluid")
+    sim.init_equilibrium(*(torch.as_tensor(fields[k], dtype=torch.float32)
+                           for k in ("rho", "ux", "uy")))
+    sim.step(3)
+    per = time_steps(sim, steps, torch) / steps
+    sim.close()
+    n = L * L
+    gbs = 72 * n / (per * 1e-3) / 1e9
+    return {"mlups": round(n / (per * 1e-3) / 1e6, 1), "ms_per_step": round(per, 5),
+            "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
 
 
 def d3q19_measure(torch, inp, steps, peak):
@@ -409,7 +466,7 @@ class OracleBand:
     periodic band of `rows` rows of the Taylor-Green workload (prescribed u~ evaluated
     at the band's global coordinates), with `threads` OpenMP threads."""
 
-    def __init__(self, rows: int, threads: int):
+    def __init__(self, rows: int, threads: int, method=None, mode=None):
         import numpy as np
 
         import oracle
@@ -426,11 +483,13 @@ class OracleBand:
         self.work = np.empty_like(self.f)
         self.ut0 = np.stack([np.cos(k * y) * np.ones((1, L)), np.sin(k * x) * np.ones((rows, 1))])
         self.s = np.array(S_RATES, float)
+        self.method = oracle.METHOD_DEFINITION if method is None else method
+        self.mode = oracle.MODE_PRESCRIBED if mode is None else mode
 
     def step(self) -> float:
         t0 = time.perf_counter()
-        self.oracle.run_inplace(self.f, self.work, 1.0, self.s, self.oracle.MODE_PRESCRIBED, 1,
-                                t0=self.t, method=self.oracle.METHOD_DEFINITION, ut0=self.ut0,
+        self.oracle.run_inplace(self.f, self.work, 1.0, self.s, self.mode, 1,
+                                t0=self.t, method=self.method, ut0=self.ut0,
                                 amp=UT_AMP, period=UT_PERIOD, nthreads=self.threads)
         self.t += 1
         return time.perf_counter() - t0
@@ -443,23 +502,45 @@ def _oracle_threads():
     return (os.cpu_count() or 1) if oracle.openmp_enabled() else 1
 
 
-def _calibrated_rows(threads: int, seconds_per_step: float) -> int:
-    probe = OracleBand(16, threads)
+def _calibrated_rows(threads: int, seconds_per_step: float, **kw) -> int:
+    probe = OracleBand(16, threads, **kw)
     probe.step()
     rate = 16 * L / probe.step()  # nodes per second
     return int(max(1, min(L, seconds_per_step * rate / L)))
 
 
-def cpu_baseline_measure(target_s: float = 15.0):
+def _band_mlups(threads: int, seconds: float, **kw):
+    """Oracle MLUPS on a band sized for `seconds` of work; when the whole lattice takes
+    less, whole-lattice steps are repeated until `seconds` have passed."""
+    rows = _calibrated_rows(threads, seconds, **kw)
+    band = OracleBand(rows, threads, **kw)
+    dt, steps = 0.0, 0
+    while steps == 0 or dt < 0.8 * seconds:
+        dt += band.step()
+        steps += 1
+    return rows * L * steps / dt / 1e6, (rows, steps), dt
+
+
+def cpu_baseline_measure(target_s: float = 12.0):
+    """The FP64 definition oracle on all host cores (the reported baseline), plus two
+    context rows: the same oracle on one core, and the fixed-moment MRT oracle (u~ = 0)
+    on all cores."""
+    import oracle
+
     threads = _oracle_threads()
-    rows = _calibrated_rows(threads, target_s)
-    band = OracleBand(rows, threads)
-    dt = band.step()
-    return {"value": round(rows * L / dt / 1e6, 3), "unit": "MLUPS", "cores": threads,
+    value, (rows, steps), dt = _band_mlups(threads, target_s)
+    one, _, _ = _band_mlups(1, 3.0)
+    mrt, (mrt_rows, mrt_steps), _ = _band_mlups(threads, 3.0, method=oracle.METHOD_MRT,
+                                                mode=oracle.MODE_ZERO)
+    return {"value": round(value, 3), "unit": "MLUPS", "cores": threads,
             "kind": "oracle",
-            "sample": (f"one time step of a {L}x{rows} periodic band of the 4096^2 "
-                       f"Taylor-Green workload, FP64 definition oracle (per-node M(u~) "
-                       f"and LU solve), {dt:.1f} s")}
+            "sample": (f"{steps} time step(s) of a {L}x{rows} periodic band of the 4096^2 "
+                       f"Taylor-Green workload, prescribed u~, FP64 definition oracle "
+                       f"(per-node M(u~) and LU solve), {dt:.1f} s"),
+            "single_core_mlups": round(one, 3),
+            "plain_mrt_oracle_mlups": round(mrt, 3),
+            "plain_mrt_sample": (f"{mrt_steps} step(s) of a {L}x{mrt_rows} band, fixed-moment "
+                                 f"MRT oracle, u~ = 0, all cores")}
 
 
 def reference_arm(args):
@@ -504,6 +585,8 @@ def main():
                     help="population storage of the timed run (profiling captures)")
     ap.add_argument("--mode", default="prescribed", choices=["zero", "fluid", "prescribed"],
                     help="relative velocity of the timed run (profiling captures)")
+    ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d3q19"],
+                    help="lattice of the timed run (d3q19: --size is the cube side)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -79,6 +79,13 @@ extern "C" {
  * its shifting matrix is lower triangular with T(u~)^{-1} = T(-u~), as for D2Q9. */
 #define LBMRV_D2Q9 0
 #define LBMRV_D3Q19 1
+/* D2Q9 with Geier's cascaded basis 1, X, Y, X^2+Y^2, X^2-Y^2, XY, XY^2, X^2Y, X^2Y^2
+ * (relation (polgeier), divided by lambda^degree from degree 2 on; rates s[0..8] in this
+ * order) and the product-form equilibrium whose moments in the fluid frame are those of
+ * the Maxwellian, rho (1, 0, 0, 2 c^2, 0, 0, 0, 0, c^4), c^2 = lambda^2/3. With
+ * LBMRV_UT_FLUID this is Geier's cascaded scheme (proposition of Section 1.3, Appendix B);
+ * the other u~ modes apply as for LBMRV_D2Q9. No adjoint. */
+#define LBMRV_D2Q9_CASCADED 2
 
 /* Choice of the relative velocity u~ (Section 1.2, Introduction). */
 #define LBMRV_UT_ZERO 0       /* u~ = 0: d'Humieres MRT */
@@ -100,12 +107,12 @@ LBMRV_API int lbmrv_version(void);
 LBMRV_API int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int storage);
 
 /* Create a simulation handle on the current CUDA device.
- *   lattice  LBMRV_D2Q9 or LBMRV_D3Q19.
+ *   lattice  LBMRV_D2Q9, LBMRV_D2Q9_CASCADED or LBMRV_D3Q19.
  *   dims     {nx, ny, 1} or {nx, ny, nz}, all >= 1, n < 2^31.
  *   lambda   velocity scale lambda > 0 (relation (lambda)).
  *   s        q relaxation rates in basis order: for D2Q9 the moment order of relation
- *            (mom): rho, q_x, q_y, e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps; for D3Q19 the
- *            order of the 3D basis above. The 1 + d conserved rates must be 0 (Section
+ *            (mom): rho, q_x, q_y, e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps; for the other
+ *            lattices the order of their bases above. The 1 + d conserved rates must be 0 (Section
  *            1.1); the others are finite.
  *   umode    LBMRV_UT_* (prescribed mode: see lbmrv_set_utilde; default A = 0).
  *   storage  LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16.
@@ -138,11 +145,12 @@ LBMRV_API int lbmrv_set_reference(lbmrv_t h, double rho_ref, const double* u_ref
 /* Change the stream later work is enqueued on. */
 LBMRV_API int lbmrv_set_stream(lbmrv_t h, void* stream);
 
-/* Kernel variant of the fused step: 0 chooses automatically (the widest aligned pack of
- * at most 4 nodes that divides nx), 1 forces one node per thread (any lattice), 2/4/8 force that many
- * consecutive nodes per thread with vector loads (must divide nx; at most 4 for FP32,
- * 8 for FP16/BF16; the state buffers must be aligned to the pack). All variants compute
- * the same values; this exists for testing and tuning. */
+/* Kernel variant of the fused step: 0 chooses automatically (the widest aligned pack that
+ * divides nx, up to the width measured fastest for the lattice and storage), 1 forces one node per thread (any lattice), 2/4/8 force that many
+ * consecutive nodes per thread with vector loads (must divide nx; at most 4 for FP32 and
+ * for D3Q19, 8 for 16-bit D2Q9; the state buffers must be aligned to the pack). All
+ * variants compute the same values; this exists for testing and tuning. It also sets the
+ * width (1, 2 or 4) of the adjoint kernel. */
 LBMRV_API int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread);
 
 /* Prescribed relative velocity u~(x, t) = amplitude * u~0(x) * cos(2 pi t / period),

@@ -6,6 +6,6 @@ a small torch-owned-memory wrapper. The CUDA library is built in-tree by ``build
 """
 from . import binding
 from .binding import LbmrvError
-from .simulation import D2Q9, D3Q19
+from .simulation import D2Q9, D2Q9Cascaded, D3Q19
 
-__all__ = ["binding", "LbmrvError", "D2Q9", "D3Q19"]
+__all__ = ["binding", "LbmrvError", "D2Q9", "D2Q9Cascaded", "D3Q19"]

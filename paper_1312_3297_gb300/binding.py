@@ -23,6 +23,7 @@ LBMRV_E_UNSUPPORTED = -6
 
 LBMRV_D2Q9 = 0
 LBMRV_D3Q19 = 1
+LBMRV_D2Q9_CASCADED = 2
 LBMRV_UT_ZERO = 0
 LBMRV_UT_FLUID = 1
 LBMRV_UT_PRESCRIBED = 2

@@ -14,7 +14,37 @@ namespace {
 // Fused step, one node per thread. Works for every lattice size (ragged rows, nx or
 // ny equal to 1 or 2). Relation (transport) in pull form: node (x, y) reads population
 // j from (x - cx_j, y - cy_j), periodic.
-template <typename T, int UM>
+// BASIS 0: the orthogonal moments of relation (mom); 1: Geier's basis (relax_node_geier).
+// For BASIS 0 the relaxation takes u~ = q / rho itself (UM_FLUID) and ignores u~ for
+// UM_ZERO, so only the prescribed modes evaluate relative_velocity first.
+template <int BASIS, int UM, int RCP>
+__device__ __forceinline__ void relax_basis(float g[9], float ux, float uy, const Rates& s,
+                                            const StoreRef& ref) {
+    if constexpr (BASIS == 0)
+        relax_node<UM, RCP>(g, ux, uy, s, ref);
+    else
+        relax_node_geier(g, ux, uy, s, ref);
+}
+
+template <int BASIS, int UM>
+constexpr bool needs_utilde() {
+    return BASIS != 0 || UM == UM_ANALYTIC || UM == UM_FIELD;
+}
+
+// Form of 1/rho per kernel variant, measured fastest on GB300 (see recip): the
+// approximation for FP32 storage, the correctly rounded one for 16-bit storage with one
+// node per relaxation call; for the paired 8-node packs the fast division, except without
+// a shift (u~ = 0).
+template <typename T>
+constexpr int scalar_rcp() {
+    return sizeof(T) == 4 ? RCP_APPROX : RCP_RN;
+}
+template <int UM>
+constexpr int paired_rcp() {
+    return UM == UM_ZERO ? RCP_RN : RCP_DIV;
+}
+
+template <typename T, int UM, int BASIS>
 __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
                                                      T* __restrict__ dst, StepArgs a) {
     const int nx = a.nx, ny = a.ny;
@@ -37,9 +67,10 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
         g[6] = to_f(src[6 * n + rm + xp]);
         g[7] = to_f(src[7 * n + rp + xp]);
         g[8] = to_f(src[8 * n + rp + xm]);
-        float ux, uy;
-        relative_velocity<UM>(g, a.ref, x, y, r0 + x, a, ux, uy);
-        relax_node(g, ux, uy, a.s, a.ref);
+        float ux = 0.0f, uy = 0.0f;
+        if constexpr (needs_utilde<BASIS, UM>())
+            relative_velocity<UM>(g, a.ref, x, y, r0 + x, a, ux, uy);
+        relax_basis<BASIS, UM, scalar_rcp<T>()>(g, ux, uy, a.s, a.ref);
 #pragma unroll
         for (int j = 0; j < 9; ++j) dst[j * n + r0 + x] = from_f<T>(g[j]);
     }
@@ -48,7 +79,7 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 // --------------------------------------------------------------------------------------
 // Fused step, NV consecutive nodes of a row per thread with aligned vector loads and
 // stores (requires nx % NV == 0 and 16-byte aligned planes); row loads in pull.cuh.
-template <typename T, int NV, int UM>
+template <typename T, int NV, int UM, int BASIS>
 __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                                                   T* __restrict__ dst, StepArgs a) {
     const int nx = a.nx, ny = a.ny;
@@ -68,21 +99,46 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                 ux_row = a.amp_t * cospif(a.two_over_ny * (float)y);
                 load_pack<float, NV>(a.sin_x + p.x0, true, sx);
             }
+            if constexpr (BASIS == 0 && NV >= 8) {
+                // Two nodes per packed FP32 instruction. With 8-node packs (16-bit storage)
+                // the step is issue-bound and pairing removes about a third of its
+                // instructions; with 4 or fewer nodes per thread the broadcast constants'
+                // extra registers cost more occupancy than the pairing saves (measured).
 #pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                float h[9];
+                for (int k = 0; k < NV; k += 2) {
+                    F2 h[9];
 #pragma unroll
-                for (int j = 0; j < 9; ++j) h[j] = g[j][k];
-                float ux, uy;
-                if (UM == UM_ANALYTIC) {
-                    ux = ux_row;
-                    uy = a.amp_t * sx[k];
-                } else {
-                    relative_velocity<UM>(h, a.ref, p.x0 + k, y, r0 + p.x0 + k, a, ux, uy);
+                    for (int j = 0; j < 9; ++j) h[j] = pack2(g[j][k], g[j][k + 1]);
+                    F2 ux(0.0f), uy(0.0f);
+                    if constexpr (UM == UM_ANALYTIC) {
+                        ux = F2(ux_row);
+                        uy = F2(a.amp_t) * pack2(sx[k], sx[k + 1]);
+                    } else if constexpr (UM == UM_FIELD) {
+                        const int64_t i = r0 + p.x0 + k;
+                        ux = F2(a.amp_t) * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
+                        uy = F2(a.amp_t) * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
+                    }
+                    relax_node<UM, paired_rcp<UM>()>(h, ux, uy, a.s, a.ref);
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) unpack2(h[j], g[j][k], g[j][k + 1]);
                 }
-                relax_node(h, ux, uy, a.s, a.ref);
+            } else {
 #pragma unroll
-                for (int j = 0; j < 9; ++j) g[j][k] = h[j];
+                for (int k = 0; k < NV; ++k) {
+                    float h[9];
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) h[j] = g[j][k];
+                    float ux = 0.0f, uy = 0.0f;
+                    if constexpr (UM == UM_ANALYTIC) {
+                        ux = ux_row;
+                        uy = a.amp_t * sx[k];
+                    } else if constexpr (needs_utilde<BASIS, UM>()) {
+                        relative_velocity<UM>(h, a.ref, p.x0 + k, y, r0 + p.x0 + k, a, ux, uy);
+                    }
+                    relax_basis<BASIS, UM, scalar_rcp<T>()>(h, ux, uy, a.s, a.ref);
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) g[j][k] = h[j];
+                }
             }
 #pragma unroll
             for (int j = 0; j < 9; ++j) store_pack<T, NV>(dst + j * n + r0 + p.x0, g[j]);
@@ -96,6 +152,30 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
 // - 3/2 |v|^2, velocities in units of lambda.
 __constant__ int kCX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __constant__ int kCY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+
+// Product-form factor of Geier's equilibrium: phi(0, a) = 2/3 - a^2,
+// phi(+-1, a) = (1/3 + a^2 +- a) / 2 (a in units of lambda).
+__device__ __forceinline__ float phi1(int c, float a) {
+    return c == 0 ? (2.0f / 3.0f - a * a) : 0.5f * ((1.0f / 3.0f + a * a) + (float)c * a);
+}
+
+template <typename T>
+__global__ void k_init_eq_product(T* __restrict__ dst, const float* __restrict__ rho,
+                                  const float* __restrict__ u, int64_t n, StoreRef ref,
+                                  float inv_lambda) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float r = rho ? rho[i] : 1.0f;
+        const float ux = u ? u[i] * inv_lambda : 0.0f;
+        const float uy = u ? u[n + i] * inv_lambda : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 9; ++j) {
+            const int cx = kCX[j], cy = kCY[j];
+            dst[j * n + i] = from_f<T>(r * phi1(cx, ux) * phi1(cy, uy) -
+                                       ref.rho * phi1(cx, ref.ux) * phi1(cy, ref.uy));
+        }
+    }
+}
 
 template <typename T>
 __global__ void k_init_eq(T* __restrict__ dst, const float* __restrict__ rho,
@@ -233,7 +313,7 @@ int grid_for(int64_t n, int threads) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
-template <typename T, int UM>
+template <typename T, int UM, int BASIS>
 cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
                              int nv) {
     const T* s = static_cast<const T*>(src);
@@ -241,17 +321,17 @@ cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cuda
     const int gy = a.ny < 65535 ? a.ny : 65535;
     if (nv == 1) {
         dim3 grid((a.nx + 255) / 256, gy);
-        k_step_scalar<T, UM><<<grid, 256, 0, st>>>(s, d, a);
+        k_step_scalar<T, UM, BASIS><<<grid, 256, 0, st>>>(s, d, a);
     } else if (nv == 2) {
         dim3 grid(((a.nx / 2) + 127) / 128, gy);
-        k_step_vec<T, 2, UM><<<grid, 128, 0, st>>>(s, d, a);
+        k_step_vec<T, 2, UM, BASIS><<<grid, 128, 0, st>>>(s, d, a);
     } else if (nv == 4) {
         dim3 grid(((a.nx / 4) + 127) / 128, gy);
-        k_step_vec<T, 4, UM><<<grid, 128, 0, st>>>(s, d, a);
+        k_step_vec<T, 4, UM, BASIS><<<grid, 128, 0, st>>>(s, d, a);
     } else if (nv == 8) {
         if constexpr (sizeof(T) == 2) {
             dim3 grid(((a.nx / 8) + 127) / 128, gy);
-            k_step_vec<T, 8, UM><<<grid, 128, 0, st>>>(s, d, a);
+            k_step_vec<T, 8, UM, BASIS><<<grid, 128, 0, st>>>(s, d, a);
         } else {
             return cudaErrorInvalidValue;
         }
@@ -261,23 +341,31 @@ cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cuda
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int BASIS>
 cudaError_t step_dispatch_um(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
                              int um, int nv) {
     switch (um) {
-        case UM_ZERO: return step_dispatch_nv<T, UM_ZERO>(src, dst, a, st, nv);
-        case UM_FLUID: return step_dispatch_nv<T, UM_FLUID>(src, dst, a, st, nv);
-        case UM_ANALYTIC: return step_dispatch_nv<T, UM_ANALYTIC>(src, dst, a, st, nv);
-        case UM_FIELD: return step_dispatch_nv<T, UM_FIELD>(src, dst, a, st, nv);
+        case UM_ZERO: return step_dispatch_nv<T, UM_ZERO, BASIS>(src, dst, a, st, nv);
+        case UM_FLUID: return step_dispatch_nv<T, UM_FLUID, BASIS>(src, dst, a, st, nv);
+        case UM_ANALYTIC: return step_dispatch_nv<T, UM_ANALYTIC, BASIS>(src, dst, a, st, nv);
+        case UM_FIELD: return step_dispatch_nv<T, UM_FIELD, BASIS>(src, dst, a, st, nv);
         default: return cudaErrorInvalidValue;
     }
+}
+
+template <typename T>
+cudaError_t step_dispatch_basis(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
+                                int um, int nv, int basis) {
+    return basis == 0 ? step_dispatch_um<T, 0>(src, dst, a, st, um, nv)
+                      : step_dispatch_um<T, 1>(src, dst, a, st, um, nv);
 }
 
 }  // namespace
 
 int step_vector_width(int storage, int nx) {
-    // Widest pack that divides nx: 16-byte packs, i.e. 4 nodes for FP32 and 8 for the
-    // 16-bit types (measured fastest on GB300 with pairwise 16-bit conversions).
+    // Widest pack that divides nx, up to the width measured fastest on GB300 (8192^2 sweep):
+    // 4 nodes for FP32 (16-byte packs), 8 for FP16 and BF16 (16-byte packs, relaxed in
+    // pairs).
     const int widest = storage == kStoreF32 ? 4 : 8;
     for (int nv = widest; nv > 1; nv >>= 1)
         if (nx % nv == 0 && nx >= nv) return nv;
@@ -285,18 +373,38 @@ int step_vector_width(int storage, int nx) {
 }
 
 cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
-                        const StepArgs& a, cudaStream_t st) {
+                        const StepArgs& a, cudaStream_t st, int basis) {
     switch (storage) {
-        case kStoreF32: return step_dispatch_um<float>(src, dst, a, st, um, nv);
-        case kStoreF16: return step_dispatch_um<__half>(src, dst, a, st, um, nv);
-        case kStoreBF16: return step_dispatch_um<__nv_bfloat16>(src, dst, a, st, um, nv);
+        case kStoreF32: return step_dispatch_basis<float>(src, dst, a, st, um, nv, basis);
+        case kStoreF16: return step_dispatch_basis<__half>(src, dst, a, st, um, nv, basis);
+        case kStoreBF16:
+            return step_dispatch_basis<__nv_bfloat16>(src, dst, a, st, um, nv, basis);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
-                           const StoreRef& rho_ref, float inv_lambda, cudaStream_t st) {
+                           const StoreRef& rho_ref, float inv_lambda, cudaStream_t st,
+                           int basis) {
     const int g = grid_for(n, 256);
+    if (basis == 1) {
+        switch (storage) {
+            case kStoreF32:
+                k_init_eq_product<float><<<g, 256, 0, st>>>(static_cast<float*>(dst), rho, u, n,
+                                                            rho_ref, inv_lambda);
+                break;
+            case kStoreF16:
+                k_init_eq_product<__half><<<g, 256, 0, st>>>(static_cast<__half*>(dst), rho, u, n,
+                                                             rho_ref, inv_lambda);
+                break;
+            case kStoreBF16:
+                k_init_eq_product<__nv_bfloat16><<<g, 256, 0, st>>>(
+                    static_cast<__nv_bfloat16*>(dst), rho, u, n, rho_ref, inv_lambda);
+                break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (storage) {
         case kStoreF32:
             k_init_eq<float><<<g, 256, 0, st>>>(static_cast<float*>(dst), rho, u, n, rho_ref,

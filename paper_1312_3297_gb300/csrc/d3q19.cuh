@@ -66,107 +66,148 @@ LBMRV_HD NodeMoments3 node_moments3(const float g[19]) {
     return m;
 }
 
-// The relaxation at one node, in place on the deviations g, for u = u~ / lambda.
-LBMRV_HD void relax_node3(float g[19], float ux, float uy, float uz, const Rates3& s,
+// The relaxation, in place on the deviations g of one node (R = float) or of two nodes
+// (R = F2, one per lane), for u = u~ / lambda. UM = UM_FLUID takes u~ = q / rho of the
+// state being relaxed (ux, uy, uz are outputs then); UM = UM_ZERO is the fixed-frame scheme.
+template <int UM, typename R>
+LBMRV_HD void relax_node3(R g[19], R& ux, R& uy, R& uz, const Rates3& s,
                           const StoreRef3& ref) {
-    const NodeMoments3 mo = node_moments3(g);
-    const float ir = recip(ref.rho + mo.drho);
-    const float jx = ref.jx + mo.jx, jy = ref.jy + mo.jy, jz = ref.jz + mo.jz;
-    const float jxx = jx * jx * ir, jyy = jy * jy * ir, jzz = jz * jz * ir;
-    const float third = 1.0f / 3.0f, ninth = 1.0f / 9.0f;
+    // Sums and differences of opposite populations.
+    const R a1 = g[1] + g[2], b1 = g[1] - g[2], a3 = g[3] + g[4], b3 = g[3] - g[4];
+    const R a5 = g[5] + g[6], b5 = g[5] - g[6];
+    const R a7 = g[7] + g[8], b7 = g[7] - g[8], a9 = g[9] + g[10], b9 = g[9] - g[10];
+    const R a11 = g[11] + g[12], b11 = g[11] - g[12], a13 = g[13] + g[14], b13 = g[13] - g[14];
+    const R a15 = g[15] + g[16], b15 = g[15] - g[16], a17 = g[17] + g[18], b17 = g[17] - g[18];
+    const R exy = a7 + a9, exz = a11 + a13, eyz = a15 + a17;   // edge sums
+    const R xe = b7 + b9, ye = b7 - b9;     // x-y edges: sum cx (= X Y^2), sum cy (= Y X^2)
+    const R xz = b11 + b13, zx = b11 - b13; // x-z edges: sum cx (= X Z^2), sum cz (= Z X^2)
+    const R yz = b15 + b17, zy = b15 - b17; // y-z edges: sum cy (= Y Z^2), sum cz (= Z Y^2)
+    // Conserved moments.
+    const R drho = (g[0] + ((a1 + a3) + a5)) + ((exy + exz) + eyz);
+    const R mjx = b1 + (xe + xz), mjy = b3 + (ye + yz), mjz = b5 + (zx + zy);
+    const R ir = recip<RCP_RN>(R(ref.rho) + drho);  // the form measured fastest in 3D
+    const R jx = R(ref.jx) + mjx, jy = R(ref.jy) + mjy, jz = R(ref.jz) + mjz;
+    const R vx = jx * ir, vy = jy * ir, vz = jz * ir;
+    if constexpr (UM == UM_FLUID) {
+        ux = vx;
+        uy = vy;
+        uz = vz;
+    }
+    const R kx = jx * vx, ky = jy * vy, kz = jz * vz;  // jx^2 / rho, ...
+    const R third = R(1.0f / 3.0f);
 
-    // Raw moments of g (deviation part) and d = m(0) - m_eq(0) of the 15 non-conserved
-    // monomials. m_eq of the D3Q19 second-order equilibrium: XX: rho/3 + jx^2/rho,
-    // XY: jx jy / rho, XY^2: jx/3, X^2Y^2: rho/9 + ((jx^2 + jy^2)/3 - jz^2/6)/rho.
-    const float exy = (g[7] + g[8]) + (g[9] + g[10]);
-    const float exz = (g[11] + g[12]) + (g[13] + g[14]);
-    const float eyz = (g[15] + g[16]) + (g[17] + g[18]);
-    const float d_xx = ((g[1] + g[2]) + exy + exz) - third * mo.drho + ref.qxx - jxx;
-    const float d_yy = ((g[3] + g[4]) + exy + eyz) - third * mo.drho + ref.qyy - jyy;
-    const float d_zz = ((g[5] + g[6]) + exz + eyz) - third * mo.drho + ref.qzz - jzz;
-    const float d_xy = ((g[7] + g[8]) - (g[9] + g[10])) + ref.qxy - jx * jy * ir;
-    const float d_xz = ((g[11] + g[12]) - (g[13] + g[14])) + ref.qxz - jx * jz * ir;
-    const float d_yz = ((g[15] + g[16]) - (g[17] + g[18])) + ref.qyz - jy * jz * ir;
-    const float d_xyy = ((g[7] - g[8]) + (g[9] - g[10])) - third * mo.jx;
-    const float d_xzz = ((g[11] - g[12]) + (g[13] - g[14])) - third * mo.jx;
-    const float d_yxx = ((g[7] - g[8]) - (g[9] - g[10])) - third * mo.jy;
-    const float d_yzz = ((g[15] - g[16]) + (g[17] - g[18])) - third * mo.jy;
-    const float d_zxx = ((g[11] - g[12]) - (g[13] - g[14])) - third * mo.jz;
-    const float d_zyy = ((g[15] - g[16]) - (g[17] - g[18])) - third * mo.jz;
-    const float d_xxyy = exy - ninth * mo.drho + ref.qxxyy - (third * (jxx + jyy) - (1.0f / 6.0f) * jzz);
-    const float d_xxzz = exz - ninth * mo.drho + ref.qxxzz - (third * (jxx + jzz) - (1.0f / 6.0f) * jyy);
-    const float d_yyzz = eyz - ninth * mo.drho + ref.qyyzz - (third * (jyy + jzz) - (1.0f / 6.0f) * jxx);
+    // d = m(0) - m_eq(0) of the 15 non-conserved monomials. m_eq of the D3Q19 second-order
+    // equilibrium: XX: rho/3 + jx^2/rho, XY: jx jy / rho, XY^2: jx/3,
+    // X^2Y^2: rho/9 + ((jx^2 + jy^2)/3 - jz^2/6)/rho = rho/9 + |j|^2/(3 rho) - jz^2/(2 rho).
+    const R t3 = third * drho;
+    const R base = fma_(third, (kx + ky) + kz, R(1.0f / 9.0f) * drho);
+    const R d_xx = ((a1 + exy) + exz) - ((t3 + kx) - R(ref.qxx));
+    const R d_yy = ((a3 + exy) + eyz) - ((t3 + ky) - R(ref.qyy));
+    const R d_zz = ((a5 + exz) + eyz) - ((t3 + kz) - R(ref.qzz));
+    const R d_xy = (a7 - a9) - fma_(jx, vy, R(-ref.qxy));
+    const R d_xz = (a11 - a13) - fma_(jx, vz, R(-ref.qxz));
+    const R d_yz = (a15 - a17) - fma_(jy, vz, R(-ref.qyz));
+    const R m3 = R(-1.0f / 3.0f);
+    const R d_xyy = fma_(m3, mjx, xe), d_xzz = fma_(m3, mjx, xz);
+    const R d_yxx = fma_(m3, mjy, ye), d_yzz = fma_(m3, mjy, yz);
+    const R d_zxx = fma_(m3, mjz, zx), d_zyy = fma_(m3, mjz, zy);
+    const R d_xxyy = (exy + R(ref.qxxyy)) - fma_(R(-0.5f), kz, base);
+    const R d_xxzz = (exz + R(ref.qxxzz)) - fma_(R(-0.5f), ky, base);
+    const R d_yyzz = (eyz + R(ref.qyyzz)) - fma_(R(-0.5f), kx, base);
 
-    // Forward shift T(u~): binomial expansion, lower non-conserved degrees only.
-    const float k_xyy = d_xyy - 2.0f * uy * d_xy - ux * d_yy;
-    const float k_xzz = d_xzz - 2.0f * uz * d_xz - ux * d_zz;
-    const float k_yxx = d_yxx - 2.0f * ux * d_xy - uy * d_xx;
-    const float k_yzz = d_yzz - 2.0f * uz * d_yz - uy * d_zz;
-    const float k_zxx = d_zxx - 2.0f * ux * d_xz - uz * d_xx;
-    const float k_zyy = d_zyy - 2.0f * uy * d_yz - uz * d_yy;
-    const float k_xxyy = d_xxyy - 2.0f * uy * d_yxx - 2.0f * ux * d_xyy + uy * uy * d_xx +
-                         ux * ux * d_yy + 4.0f * ux * uy * d_xy;
-    const float k_xxzz = d_xxzz - 2.0f * uz * d_zxx - 2.0f * ux * d_xzz + uz * uz * d_xx +
-                         ux * ux * d_zz + 4.0f * ux * uz * d_xz;
-    const float k_yyzz = d_yyzz - 2.0f * uz * d_zyy - 2.0f * uy * d_yzz + uz * uz * d_yy +
-                         uy * uy * d_zz + 4.0f * uy * uz * d_yz;
+    // Relaxation of the second order, diagonal in (trace, X^2-Y^2, Y^2-Z^2, XY, XZ, YZ).
+    const R rt = R(s.e) * ((d_xx + d_yy) + d_zz);
+    const R ra = R(s.a) * (d_xx - d_yy), rb = R(s.b) * (d_yy - d_zz);
+    const R rtb = rt + rb;
+    const R r_xx = third * fma_(R(2.0f), ra, rtb);
+    const R r_yy = third * (rtb - ra);
+    const R r_zz = third * (rt - fma_(R(2.0f), rb, ra));
+    const R r_xy = R(s.xy) * d_xy, r_xz = R(s.xz) * d_xz, r_yz = R(s.yz) * d_yz;
 
-    // Relaxation S, diagonal in the basis polynomials.
-    const float tr = d_xx + d_yy + d_zz, da = d_xx - d_yy, db = d_yy - d_zz;
-    const float rt = s.e * tr, ra = s.a * da, rb = s.b * db;
-    const float r_xx = third * (rt + 2.0f * ra + rb);
-    const float r_yy = third * (rt - ra + rb);
-    const float r_zz = third * (rt - ra - 2.0f * rb);
-    const float r_xy = s.xy * d_xy, r_xz = s.xz * d_xz, r_yz = s.yz * d_yz;
-    const float r_xyy = s.xyy * k_xyy, r_xzz = s.xzz * k_xzz, r_yxx = s.yxx * k_yxx;
-    const float r_yzz = s.yzz * k_yzz, r_zxx = s.zxx * k_zxx, r_zyy = s.zyy * k_zyy;
-    const float r_xxyy = s.xxyy * k_xxyy, r_xxzz = s.xxzz * k_xxzz, r_yyzz = s.yyzz * k_yyzz;
-
-    // Back shift T(-u~) (morphism).
-    const float h_xyy = r_xyy + 2.0f * uy * r_xy + ux * r_yy;
-    const float h_xzz = r_xzz + 2.0f * uz * r_xz + ux * r_zz;
-    const float h_yxx = r_yxx + 2.0f * ux * r_xy + uy * r_xx;
-    const float h_yzz = r_yzz + 2.0f * uz * r_yz + uy * r_zz;
-    const float h_zxx = r_zxx + 2.0f * ux * r_xz + uz * r_xx;
-    const float h_zyy = r_zyy + 2.0f * uy * r_yz + uz * r_yy;
-    const float h_xxyy = r_xxyy + 2.0f * uy * r_yxx + 2.0f * ux * r_xyy + uy * uy * r_xx +
-                         ux * ux * r_yy + 4.0f * ux * uy * r_xy;
-    const float h_xxzz = r_xxzz + 2.0f * uz * r_zxx + 2.0f * ux * r_xzz + uz * uz * r_xx +
-                         ux * ux * r_zz + 4.0f * ux * uz * r_xz;
-    const float h_yyzz = r_yyzz + 2.0f * uz * r_zyy + 2.0f * uy * r_yzz + uz * uz * r_yy +
-                         uy * uy * r_zz + 4.0f * uy * uz * r_yz;
+    R h_xyy, h_xzz, h_yxx, h_yzz, h_zxx, h_zyy, h_xxyy, h_xxzz, h_yyzz;
+    if constexpr (UM == UM_ZERO) {
+        h_xyy = R(s.xyy) * d_xyy;
+        h_xzz = R(s.xzz) * d_xzz;
+        h_yxx = R(s.yxx) * d_yxx;
+        h_yzz = R(s.yzz) * d_yzz;
+        h_zxx = R(s.zxx) * d_zxx;
+        h_zyy = R(s.zyy) * d_zyy;
+        h_xxyy = R(s.xxyy) * d_xxyy;
+        h_xxzz = R(s.xxzz) * d_xxzz;
+        h_yyzz = R(s.yyzz) * d_yyzz;
+    } else {
+        const R ux2 = ux + ux, uy2 = uy + uy, uz2 = uz + uz;
+        const R uxx = ux * ux, uyy = uy * uy, uzz = uz * uz;
+        const R uxy4 = ux2 * uy2, uxz4 = ux2 * uz2, uyz4 = uy2 * uz2;
+        // Forward shift T(u~): binomial expansion of (X - ux)^a (Y - uy)^b (Z - uz)^c,
+        // lower non-conserved degrees only.
+        const R k_xyy = d_xyy - fma_(uy2, d_xy, ux * d_yy);
+        const R k_xzz = d_xzz - fma_(uz2, d_xz, ux * d_zz);
+        const R k_yxx = d_yxx - fma_(ux2, d_xy, uy * d_xx);
+        const R k_yzz = d_yzz - fma_(uz2, d_yz, uy * d_zz);
+        const R k_zxx = d_zxx - fma_(ux2, d_xz, uz * d_xx);
+        const R k_zyy = d_zyy - fma_(uy2, d_yz, uz * d_yy);
+        const R k_xxyy = fma_(uyy, d_xx, fma_(uxx, d_yy, fma_(uxy4, d_xy, d_xxyy))) -
+                         fma_(uy2, d_yxx, ux2 * d_xyy);
+        const R k_xxzz = fma_(uzz, d_xx, fma_(uxx, d_zz, fma_(uxz4, d_xz, d_xxzz))) -
+                         fma_(uz2, d_zxx, ux2 * d_xzz);
+        const R k_yyzz = fma_(uzz, d_yy, fma_(uyy, d_zz, fma_(uyz4, d_yz, d_yyzz))) -
+                         fma_(uz2, d_zyy, uy2 * d_yzz);
+        // Relaxation S of the third and fourth orders.
+        const R r_xyy = R(s.xyy) * k_xyy, r_xzz = R(s.xzz) * k_xzz, r_yxx = R(s.yxx) * k_yxx;
+        const R r_yzz = R(s.yzz) * k_yzz, r_zxx = R(s.zxx) * k_zxx, r_zyy = R(s.zyy) * k_zyy;
+        const R r_xxyy = R(s.xxyy) * k_xxyy, r_xxzz = R(s.xxzz) * k_xxzz;
+        const R r_yyzz = R(s.yyzz) * k_yyzz;
+        // Back shift T(-u~) (morphism).
+        h_xyy = fma_(uy2, r_xy, fma_(ux, r_yy, r_xyy));
+        h_xzz = fma_(uz2, r_xz, fma_(ux, r_zz, r_xzz));
+        h_yxx = fma_(ux2, r_xy, fma_(uy, r_xx, r_yxx));
+        h_yzz = fma_(uz2, r_yz, fma_(uy, r_zz, r_yzz));
+        h_zxx = fma_(ux2, r_xz, fma_(uz, r_xx, r_zxx));
+        h_zyy = fma_(uy2, r_yz, fma_(uz, r_yy, r_zyy));
+        h_xxyy = fma_(uy2, r_yxx, fma_(ux2, r_xyy,
+                 fma_(uyy, r_xx, fma_(uxx, r_yy, fma_(uxy4, r_xy, r_xxyy)))));
+        h_xxzz = fma_(uz2, r_zxx, fma_(ux2, r_xzz,
+                 fma_(uzz, r_xx, fma_(uxx, r_zz, fma_(uxz4, r_xz, r_xxzz)))));
+        h_yyzz = fma_(uz2, r_zyy, fma_(uy2, r_yzz,
+                 fma_(uzz, r_yy, fma_(uyy, r_zz, fma_(uyz4, r_yz, r_yyzz)))));
+    }
 
     // f* = f - M(0)^{-1} h, M(0) the monomial moment matrix restricted to zero conserved
     // moments: edges from their four moments, faces from the second-order sums and the
     // momentum balance, rest from the mass balance.
-    const float ex1 = 0.5f * (h_xxyy + r_xy), ex2 = 0.5f * (h_xxyy - r_xy);
-    const float ox1 = 0.5f * (h_xyy + h_yxx), ox2 = 0.5f * (h_xyy - h_yxx);
-    g[7] -= 0.5f * (ex1 + ox1);
-    g[8] -= 0.5f * (ex1 - ox1);
-    g[9] -= 0.5f * (ex2 + ox2);
-    g[10] -= 0.5f * (ex2 - ox2);
-    const float ez1 = 0.5f * (h_xxzz + r_xz), ez2 = 0.5f * (h_xxzz - r_xz);
-    const float oz1 = 0.5f * (h_xzz + h_zxx), oz2 = 0.5f * (h_xzz - h_zxx);
-    g[11] -= 0.5f * (ez1 + oz1);
-    g[12] -= 0.5f * (ez1 - oz1);
-    g[13] -= 0.5f * (ez2 + oz2);
-    g[14] -= 0.5f * (ez2 - oz2);
-    const float ey1 = 0.5f * (h_yyzz + r_yz), ey2 = 0.5f * (h_yyzz - r_yz);
-    const float oy1 = 0.5f * (h_yzz + h_zyy), oy2 = 0.5f * (h_yzz - h_zyy);
-    g[15] -= 0.5f * (ey1 + oy1);
-    g[16] -= 0.5f * (ey1 - oy1);
-    g[17] -= 0.5f * (ey2 + oy2);
-    g[18] -= 0.5f * (ey2 - oy2);
-    const float sx = r_xx - h_xxyy - h_xxzz, sy = r_yy - h_xxyy - h_yyzz,
-                sz = r_zz - h_xxzz - h_yyzz;
-    const float mx = h_xyy + h_xzz, my = h_yxx + h_yzz, mz = h_zxx + h_zyy;
-    g[1] -= 0.5f * (sx - mx);
-    g[2] -= 0.5f * (sx + mx);
-    g[3] -= 0.5f * (sy - my);
-    g[4] -= 0.5f * (sy + my);
-    g[5] -= 0.5f * (sz - mz);
-    g[6] -= 0.5f * (sz + mz);
-    g[0] -= (h_xxyy + h_xxzz + h_yyzz) - (r_xx + r_yy + r_zz);
+    const R q4 = R(-0.25f), q2 = R(-0.5f);
+    {
+        const R p = h_xxyy + r_xy, q = h_xxyy - r_xy, o1 = h_xyy + h_yxx, o2 = h_xyy - h_yxx;
+        g[7] = fma_(q4, p + o1, g[7]);
+        g[8] = fma_(q4, p - o1, g[8]);
+        g[9] = fma_(q4, q + o2, g[9]);
+        g[10] = fma_(q4, q - o2, g[10]);
+    }
+    {
+        const R p = h_xxzz + r_xz, q = h_xxzz - r_xz, o1 = h_xzz + h_zxx, o2 = h_xzz - h_zxx;
+        g[11] = fma_(q4, p + o1, g[11]);
+        g[12] = fma_(q4, p - o1, g[12]);
+        g[13] = fma_(q4, q + o2, g[13]);
+        g[14] = fma_(q4, q - o2, g[14]);
+    }
+    {
+        const R p = h_yyzz + r_yz, q = h_yyzz - r_yz, o1 = h_yzz + h_zyy, o2 = h_yzz - h_zyy;
+        g[15] = fma_(q4, p + o1, g[15]);
+        g[16] = fma_(q4, p - o1, g[16]);
+        g[17] = fma_(q4, q + o2, g[17]);
+        g[18] = fma_(q4, q - o2, g[18]);
+    }
+    const R sx = r_xx - (h_xxyy + h_xxzz), sy = r_yy - (h_xxyy + h_yyzz);
+    const R sz = r_zz - (h_xxzz + h_yyzz);
+    const R mx = h_xyy + h_xzz, my = h_yxx + h_yzz, mz = h_zxx + h_zyy;
+    g[1] = fma_(q2, sx - mx, g[1]);
+    g[2] = fma_(q2, sx + mx, g[2]);
+    g[3] = fma_(q2, sy - my, g[3]);
+    g[4] = fma_(q2, sy + my, g[4]);
+    g[5] = fma_(q2, sz - mz, g[5]);
+    g[6] = fma_(q2, sz + mz, g[6]);
+    g[0] = g[0] - (((h_xxyy + h_xxzz) + h_yyzz) - rt);
 }
 
 }  // namespace lbmrv

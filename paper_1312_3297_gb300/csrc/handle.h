@@ -16,6 +16,7 @@ struct lbmrv_s {
     int lattice = LBMRV_D2Q9;
     int q = 9;       // populations per node
     int dim = 2;     // spatial dimensions
+    int basis = 0;   // D2Q9 moment basis: 0 orthogonal set of relation (mom), 1 Geier's set
     int umode = LBMRV_UT_ZERO;
     int storage = LBMRV_FP32;
     int device = 0;
@@ -96,12 +97,21 @@ inline StoreRef store_ref(const lbmrv_s* h) {
     ref.jy = (float)(r * uy);
     ref.ux = (float)ux;
     ref.uy = (float)uy;
-    ref.c[0] = (float)(3.0 * r * uu);             // e
-    ref.c[1] = (float)(r * (ux * ux - uy * uy));  // p_xx
-    ref.c[2] = (float)(r * ux * uy);              // p_xy
-    ref.c[3] = (float)(-r * ux);                  // q_x (3rd order)
-    ref.c[4] = (float)(-r * uy);                  // q_y (3rd order)
-    ref.c[5] = (float)(-3.0 * r * uu);            // eps
+    if (h->basis == 0) {
+        ref.c[0] = (float)(3.0 * r * uu);             // e
+        ref.c[1] = (float)(r * (ux * ux - uy * uy));  // p_xx
+        ref.c[2] = (float)(r * ux * uy);              // p_xy
+        ref.c[3] = (float)(-r * ux);                  // q_x (3rd order)
+        ref.c[4] = (float)(-r * uy);                  // q_y (3rd order)
+        ref.c[5] = (float)(-3.0 * r * uu);            // eps
+    } else {  // Geier basis, product equilibrium: monomials XX, YY, XY, XYY, YXX, XXYY
+        ref.c[0] = (float)(r * ux * ux);
+        ref.c[1] = (float)(r * uy * uy);
+        ref.c[2] = (float)(r * ux * uy);
+        ref.c[3] = (float)(r * ux * uy * uy);
+        ref.c[4] = (float)(r * uy * ux * ux);
+        ref.c[5] = (float)(r * uu / 3.0 + r * ux * ux * uy * uy);
+    }
     return ref;
 }
 

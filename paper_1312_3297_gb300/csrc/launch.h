@@ -18,12 +18,14 @@ constexpr int kReduceMaxBlocks = 152 * 8;
 int step_vector_width(int storage, int nx);
 
 // One fused step src -> dst. um: UM_* of d2q9.cuh; nv: 1 (scalar kernel) or a vector
-// width returned by step_vector_width (or any smaller power of two dividing nx).
+// width returned by step_vector_width (or any smaller power of two dividing nx); basis 0:
+// the orthogonal moments of the paper's D2Q9 example, 1: Geier's (cascaded) basis.
 cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
-                        const StepArgs& a, cudaStream_t st);
+                        const StepArgs& a, cudaStream_t st, int basis = 0);
 
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
-                           const StoreRef& ref, float inv_lambda, cudaStream_t st);
+                           const StoreRef& ref, float inv_lambda, cudaStream_t st,
+                           int basis = 0);
 
 cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, int64_t n,
                            const StoreRef& ref, float lambda, cudaStream_t st);
@@ -37,7 +39,7 @@ cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho
                              int nblk, double* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- D3Q19
-int step3_vector_width(int nx);
+int step3_vector_width(int storage, int nx);
 cudaError_t launch_step3(int storage, int um, int nv, const void* src, void* dst,
                          const StepArgs3& a, cudaStream_t st);
 cudaError_t launch_init_eq3(int storage, void* dst, const float* rho, const float* u, int64_t n,

@@ -19,8 +19,11 @@ namespace lbmrv {
 namespace {
 thread_local char g_create_err[320] = {0};
 
-int lattice_q(int lattice) { return lattice == LBMRV_D2Q9 ? 9 : (lattice == LBMRV_D3Q19 ? 19 : -1); }
-int lattice_dim(int lattice) { return lattice == LBMRV_D2Q9 ? 2 : 3; }
+int lattice_q(int lattice) {
+    if (lattice == LBMRV_D2Q9 || lattice == LBMRV_D2Q9_CASCADED) return 9;
+    return lattice == LBMRV_D3Q19 ? 19 : -1;
+}
+int lattice_dim(int lattice) { return lattice == LBMRV_D3Q19 ? 3 : 2; }
 
 // Validation shared by lbmrv_create and lbmrv_set_rates: conserved rates are 0 (Section
 // 1.1: 1 + d conserved moments), the others finite.
@@ -49,8 +52,8 @@ const char* last_create_error() { return g_create_err; }
 
 int choose_width(const lbmrv_s* h, const void* a, const void* b) {
     if (h->width > 0) return h->width;
-    const int nv = h->lattice == LBMRV_D2Q9 ? step_vector_width(h->storage, (int)h->nx)
-                                            : step3_vector_width((int)h->nx);
+    const int nv = h->dim == 2 ? step_vector_width(h->storage, (int)h->nx)
+                               : step3_vector_width(h->storage, (int)h->nx);
     const size_t align = (size_t)(nv * elem_size(h->storage));
     if (nv > 1 && ((reinterpret_cast<uintptr_t>(a) % align) != 0 ||
                    (reinterpret_cast<uintptr_t>(b) % align) != 0))
@@ -59,8 +62,9 @@ int choose_width(const lbmrv_s* h, const void* a, const void* b) {
 }
 
 cudaError_t launch_handle_step(const lbmrv_s* h, int nv, const void* src, void* dst, int64_t t) {
-    if (h->lattice == LBMRV_D2Q9)
-        return launch_step(h->storage, kernel_mode(h), nv, src, dst, make_args(h, t), h->stream);
+    if (h->dim == 2)
+        return launch_step(h->storage, kernel_mode(h), nv, src, dst, make_args(h, t), h->stream,
+                           h->basis);
     return launch_step3(h->storage, kernel_mode(h), nv, src, dst, make_args3(h, t), h->stream);
 }
 
@@ -89,7 +93,7 @@ int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda
     if (q < 0) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: bad lattice");
     if (!dims || dims[0] < 1 || dims[1] < 1)
         return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: dims must be >= 1");
-    if (lattice == LBMRV_D2Q9 && dims[2] != 1 && dims[2] != 0)
+    if (lattice != LBMRV_D3Q19 && dims[2] != 1 && dims[2] != 0)
         return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: D2Q9 dims must be {nx>=1, ny>=1, 1}");
     if (lattice == LBMRV_D3Q19 && dims[2] < 1)
         return fail(nullptr, LBMRV_E_INVAL, "lbmrv_create: D3Q19 dims must be >= 1");
@@ -119,6 +123,7 @@ int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda
     h->lattice = lattice;
     h->q = q;
     h->dim = lattice_dim(lattice);
+    h->basis = lattice == LBMRV_D2Q9_CASCADED ? 1 : 0;
     h->umode = umode;
     h->storage = storage;
     h->nx = dims[0];
@@ -199,7 +204,7 @@ int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread) {
         h->width = w;
         return LBMRV_OK;
     }
-    const int widest = h->lattice == LBMRV_D3Q19 ? 4 : (h->storage == LBMRV_FP32 ? 4 : 8);
+    const int widest = h->dim == 3 ? 4 : (h->storage == LBMRV_FP32 ? 4 : 8);
     if ((w != 2 && w != 4 && w != 8) || w > widest || h->nx % w != 0)
         return fail(h, LBMRV_E_INVAL,
                     "lbmrv_set_kernel_width: %d must be 0, 1 or a pack width (<= %d) dividing nx",
@@ -248,9 +253,9 @@ int lbmrv_init_equilibrium(lbmrv_t h, const float* rho_dev, const float* u_dev) 
     if (!u_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_init_equilibrium: u is NULL");
     DeviceGuard g(h->device);
     cudaError_t e;
-    if (h->lattice == LBMRV_D2Q9)
+    if (h->dim == 2)
         e = launch_init_eq(h->storage, h->f[h->cur], rho_dev, u_dev, h->n, store_ref(h),
-                           (float)(1.0 / h->lambda), h->stream);
+                           (float)(1.0 / h->lambda), h->stream, h->basis);
     else
         e = launch_init_eq3(h->storage, h->f[h->cur], rho_dev, u_dev, h->n, store_ref3(h),
                             (float)(1.0 / h->lambda), h->stream);
@@ -272,9 +277,9 @@ int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u
         e = cudaMemcpyAsync(stage + h->n, u_host, h->dim * nb, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_init_equilibrium_host: copy");
     const float* rho = rho_host ? stage : nullptr;
-    if (h->lattice == LBMRV_D2Q9)
+    if (h->dim == 2)
         e = launch_init_eq(h->storage, h->f[h->cur], rho, stage + h->n, h->n, store_ref(h),
-                           (float)(1.0 / h->lambda), h->stream);
+                           (float)(1.0 / h->lambda), h->stream, h->basis);
     else
         e = launch_init_eq3(h->storage, h->f[h->cur], rho, stage + h->n, h->n, store_ref3(h),
                             (float)(1.0 / h->lambda), h->stream);
@@ -300,7 +305,7 @@ int lbmrv_step(lbmrv_t h, int64_t n) {
 }
 
 static cudaError_t moments_into(lbmrv_t h, float* rho, float* u) {
-    if (h->lattice == LBMRV_D2Q9)
+    if (h->dim == 2)
         return launch_moments(h->storage, h->f[h->cur], rho, u, h->n, store_ref(h),
                               (float)h->lambda, h->stream);
     return launch_moments3(h->storage, h->f[h->cur], rho, u, h->n, store_ref3(h),
@@ -336,7 +341,7 @@ int lbmrv_conserved3(lbmrv_t h, double out_host[5]) {
     double* res = h->red + 8 * (size_t)h->red_blocks;
     cudaError_t e;
     double tmp[5] = {0, 0, 0, 0, 0};
-    if (h->lattice == LBMRV_D2Q9) {
+    if (h->dim == 2) {
         double four[4] = {0, 0, 0, 0};
         e = launch_conserved(h->storage, h->f[h->cur], h->n, h->rho_ref,
                              h->rho_ref * h->u_ref[0] / h->lambda,

@@ -218,3 +218,10 @@ class D3Q19(D2Q9):
 
     def __init__(self, nx: int, ny: int, nz: int, s, **kw):
         super().__init__(nx, ny, s, nz=nz, **kw)
+
+
+class D2Q9Cascaded(D2Q9):
+    """D2Q9 with Geier's cascaded basis and product-form equilibrium (rates in the order
+    1, X, Y, X^2+Y^2, X^2-Y^2, XY, XY^2, X^2Y, X^2Y^2). mode="fluid" is Geier's scheme."""
+
+    LATTICE = B.LBMRV_D2Q9_CASCADED

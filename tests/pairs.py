@@ -24,14 +24,25 @@ def reference_populations(rho_ref, u_ref, lam=1.0):
     return W * rho_ref * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (ux * ux + uy * uy))
 
 
+def product_populations(rho_ref, u_ref, lam=1.0):
+    """Product-form (Maxwellian-moment) equilibrium of the reference state, from its
+    definition phi(0, a) = 2/3 - a^2, phi(+-1, a) = (1/3 + a^2 +- a)/2."""
+    cx = [0, 1, 0, -1, 0, 1, -1, -1, 1]
+    cy = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    phi = lambda c, a: 2 / 3 - a * a if c == 0 else 0.5 * (1 / 3 + a * a + c * a)  # noqa
+    ux, uy = u_ref[0] / lam, u_ref[1] / lam
+    return np.array([rho_ref * phi(cx[j], ux) * phi(cy[j], uy) for j in range(9)])
+
+
 def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=None,
-            ut0=None, amp=0.0, period=0.0, width=0, u_ref=(0.0, 0.0)):
+            ut0=None, amp=0.0, period=0.0, width=0, u_ref=(0.0, 0.0), cascaded=False):
     import torch
 
-    from paper_1312_3297_gb300 import D2Q9
+    from paper_1312_3297_gb300 import D2Q9, D2Q9Cascaded
 
     rho, ux, uy = fields
-    sim = D2Q9(nx, ny, s, mode=mode, storage=storage, lam=lam, rho_ref=rho_ref, u_ref=u_ref)
+    cls = D2Q9Cascaded if cascaded else D2Q9
+    sim = cls(nx, ny, s, mode=mode, storage=storage, lam=lam, rho_ref=rho_ref, u_ref=u_ref)
     if width:
         sim.set_kernel_width(width)
     if MODES[mode] == 2:
@@ -40,7 +51,8 @@ def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=Non
     sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
     sim.step(steps)
     g = sim.state().double().cpu().numpy()
-    f = g + reference_populations(sim.rho_ref, u_ref, lam)[:, None, None]
+    ref_pop = product_populations if cascaded else reference_populations
+    f = g + ref_pop(sim.rho_ref, u_ref, lam)[:, None, None]
     r, a, b = (t.double().cpu().numpy() for t in sim.moments())
     sim.close()
     return f, (r, a, b)
@@ -51,7 +63,10 @@ def oracle_run(nx, ny, s, mode, steps, fields, lam=1.0, ut0=None, amp=0.0, perio
     import oracle
 
     rho, ux, uy = fields
-    f0 = oracle.init_equilibrium(rho, ux, uy, lam)
+    if method in (oracle.METHOD_GEIER, oracle.METHOD_CASCADED):
+        f0 = oracle.init_equilibrium_product(rho, ux, uy, lam)
+    else:
+        f0 = oracle.init_equilibrium(rho, ux, uy, lam)
     ut = None if ut0 is None else inp.to_f32_exact(ut0)
     S = oracle.post_collision_state(f0, lam, np.asarray(s, float), MODES[mode], steps,
                                     ut0=ut, amp=amp, period=period, method=method,

@@ -87,3 +87,26 @@ def test_perturbed_uniform_flow_512_crop_2000_steps(crop_oracle, storage, u_ref,
     form = "reference" if u_ref != (0.0, 0.0) else "plain"
     _report(f"{storage}-{form}-fluid-512x512-2000", e)
     assert e[1] <= tol, e
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-4), ("bf16", 1.5e-3)])
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed", "field"])
+def test_16bit_every_kernel_width(storage, tol, mode):
+    """Every variant of the 16-bit step — one node per thread, 2-, 4- and 8-node packs (the
+    8-node packs relax two nodes per packed FP32 instruction) — against the oracle, in the
+    reference form, where storage rounding stays far below what a wrong lane, term or
+    sign would cost. 72 x 21: nine 8-node packs per row (a partly idle warp), odd ny;
+    40 steps of the perturbed uniform flow."""
+    nx, ny, steps = 72, 21, 40
+    fields = f32_fields(inp.perturbed_uniform(nx, ny, seed=11, U=U_MEAN))
+    kw = dict(amp=0.03, period=50.0)
+    if mode == "field":
+        kw["ut0"] = inp.to_f32_exact(inp.prescribed_base_field(nx, ny, seed=12, smooth=False))
+    m = "prescribed" if mode == "field" else mode
+    f_o, m_o = oracle_run(nx, ny, S, m, steps, fields, **kw)
+    for w in (1, 2, 4, 8):
+        f_g, m_g = gpu_run(nx, ny, S, m, steps, fields, storage=storage, u_ref=U_MEAN,
+                           width=w, **kw)
+        e = rel_errors(f_g, m_g, f_o, m_o)
+        assert e[1] <= tol, (w, e)
+        assert e[0] <= tol, (w, e)
