@@ -35,7 +35,7 @@ WORKLOAD = ("D2Q9 relative-velocity step, FP32, 4096x4096 periodic, Taylor-Green
             "s_nu=1.8, prescribed u~ = 0.03 (cos 2pi y/L, sin 2pi x/L) cos(2pi t/1000)")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "d2q9_step_tg4096_traffic.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1312_3297_gb300", "csrc", f)
-                  for f in ("d2q9.cuh", "d2q9_kernels.cu")]
+                  for f in ("d2q9.cuh", "d2q9_kernels.cu", "pull.cuh", "f32x2.cuh")]
 
 
 def kernel_hash() -> str:
