@@ -419,7 +419,7 @@ def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
     sim.close()
     ws_gb = ws.numel() / 1e9
     del ws
-    return {"workload": "1024^2 noisy shear wave, prescribed u~, KE loss, 2000 steps, seg 45",
+    return {"workload": f"1024^2 noisy shear wave, prescribed u~, KE loss, {n_steps} steps, seg 45",
             "forward_ms_per_step": round(fwd_ms, 5),
             "adjoint_ms_per_step": round(adj_ms, 5),
             "adjoint_over_forward": round(adj_ms / fwd_ms, 3),
@@ -430,6 +430,19 @@ def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
             "gradient_over_forward_run": round(e0.elapsed_time(e3) / (fwd_ms * n_steps), 3),
             "workspace_gb": round(ws_gb, 2), "loss": ke, "dL_dsnu": ds[4] + ds[5],
             "dL_dA": da}
+
+
+def adjoint_arm(args):
+    """The adjoint workload alone (one GPU): its JSON dict on one line."""
+    import torch
+
+    import lbm_inputs as inp
+    from paper_1312_3297_gb300 import D2Q9, binding
+
+    binding.load()
+    peak, _ = measured_peaks()
+    print(json.dumps(adjoint_measure(torch, D2Q9, inp, peak, n_steps=args.adjoint_steps)),
+          flush=True)
 
 
 def e2e_measure(torch, D2Q9, inp, fields, steps):
@@ -587,11 +600,17 @@ def main():
                     help="relative velocity of the timed run (profiling captures)")
     ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d3q19"],
                     help="lattice of the timed run (d3q19: --size is the cube side)")
+    ap.add_argument("--case", default="step", choices=["step", "adjoint"],
+                    help="adjoint: only the adjoint workload's timings (profiling captures)")
+    ap.add_argument("--adjoint-steps", type=int, default=2000,
+                    help="time steps of the adjoint workload's whole-gradient run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         reference_arm(args)
+    elif args.case == "adjoint":
+        adjoint_arm(args)
     else:
         gpu_arm(args)
 

@@ -180,6 +180,25 @@ def test_time_index_and_state_roundtrip():
     a.close()
 
 
+def test_zero_steps_is_a_no_op_and_negative_counts_fail():
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9
+    from paper_1312_3297_gb300.binding import LbmrvError
+
+    rho, ux, uy = f32_fields(inp.random_sine_flow(16, 8, seed=9))
+    sim = D2Q9(16, 8, S_PAPER, mode="fluid")
+    sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+    snap = sim.state()
+    sim.step(0)
+    assert sim.time == 0
+    torch.testing.assert_close(sim.state(), snap, rtol=0, atol=0)
+    with pytest.raises(LbmrvError):
+        sim.step(-1)
+    assert sim.time == 0
+    sim.close()
+
+
 # --------------------------------------------------------------------- full size
 def _window_oracle(fields_full, center, R, steps, s, mode, amp, period, nxg, nyg):
     """Oracle of the node `center` of a periodic nxg x nyg lattice after `steps` steps,
