@@ -310,6 +310,7 @@ def gpu_arm(args):
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": recorded_traffic() if headline else None,
                          "peak_kind": peak_kind,
+                         "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                          "kernel": (f"{'k_step_vec' if args.lattice == 'd2q9' else 'k_step3'}"
                                     f"<{args.storage},{default_width(args.lattice, args.storage, size)},"
                                     f"{args.mode}>")},
@@ -355,7 +356,7 @@ def d3q19_measure(torch, inp, steps, peak):
     d = inp.taylor_green_3d(L3, L3, L3, u0=0.04)
     s3 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
     out = {}
-    for storage, bpn in (("fp32", 152), ("fp16", 76)):
+    for storage, bpn in (("fp32", 152), ("fp16", 76), ("bf16", 76)):
         sim = D3Q19(L3, L3, L3, s3, mode="fluid", storage=storage)
         sim.init_equilibrium(torch.as_tensor(d["rho"], dtype=torch.float32),
                              *(torch.as_tensor(c, dtype=torch.float32) for c in d["u"]))

@@ -146,11 +146,12 @@ LBMRV_API int lbmrv_set_reference(lbmrv_t h, double rho_ref, const double* u_ref
 LBMRV_API int lbmrv_set_stream(lbmrv_t h, void* stream);
 
 /* Kernel variant of the fused step: 0 chooses automatically (the widest aligned pack that
- * divides nx, up to the width measured fastest for the lattice and storage), 1 forces one node per thread (any lattice), 2/4/8 force that many
- * consecutive nodes per thread with vector loads (must divide nx; at most 4 for FP32 and
- * for D3Q19, 8 for 16-bit D2Q9; the state buffers must be aligned to the pack). All
- * variants compute the same values; this exists for testing and tuning. It also sets the
- * width (1, 2 or 4) of the adjoint kernel. */
+ * divides nx, up to the width measured fastest for the lattice and storage), 1 forces one
+ * node per thread (any lattice), 2/4/8 force that many consecutive nodes per thread with
+ * vector loads (must divide nx; at most 4 for FP32, 8 for 16-bit storage; the state
+ * buffers must be aligned to the pack). All variants compute the same scheme to rounding;
+ * this exists for testing and tuning. It also sets the width (1, 2 or 4) of the adjoint
+ * kernel. */
 LBMRV_API int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread);
 
 /* Prescribed relative velocity u~(x, t) = amplitude * u~0(x) * cos(2 pi t / period),

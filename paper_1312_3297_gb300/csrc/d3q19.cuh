@@ -69,7 +69,8 @@ LBMRV_HD NodeMoments3 node_moments3(const float g[19]) {
 // The relaxation, in place on the deviations g of one node (R = float) or of two nodes
 // (R = F2, one per lane), for u = u~ / lambda. UM = UM_FLUID takes u~ = q / rho of the
 // state being relaxed (ux, uy, uz are outputs then); UM = UM_ZERO is the fixed-frame scheme.
-template <int UM, typename R>
+// RCP: the form of 1/rho (see recip).
+template <int UM, int RCP = RCP_RN, typename R>
 LBMRV_HD void relax_node3(R g[19], R& ux, R& uy, R& uz, const Rates3& s,
                           const StoreRef3& ref) {
     // Sums and differences of opposite populations.
@@ -85,7 +86,7 @@ LBMRV_HD void relax_node3(R g[19], R& ux, R& uy, R& uz, const Rates3& s,
     // Conserved moments.
     const R drho = (g[0] + ((a1 + a3) + a5)) + ((exy + exz) + eyz);
     const R mjx = b1 + (xe + xz), mjy = b3 + (ye + yz), mjz = b5 + (zx + zy);
-    const R ir = recip<RCP_RN>(R(ref.rho) + drho);  // the form measured fastest in 3D
+    const R ir = recip<RCP>(R(ref.rho) + drho);
     const R jx = R(ref.jx) + mjx, jy = R(ref.jy) + mjy, jz = R(ref.jz) + mjz;
     const R vx = jx * ir, vy = jy * ir, vz = jz * ir;
     if constexpr (UM == UM_FLUID) {

@@ -13,6 +13,14 @@ namespace {
 
 constexpr int kThreads3 = 128;
 
+// Element type of a step kernel's state arguments.
+template <typename K>
+struct KernelArg;
+template <typename T>
+struct KernelArg<void (*)(const T*, T*, StepArgs3)> {
+    using type = T;
+};
+
 template <int UM>
 __device__ __forceinline__ void relative_velocity3(const float g[19], int64_t i, int64_t n,
                                                    const StepArgs3& a, float& ux, float& uy,
@@ -32,6 +40,25 @@ __device__ __forceinline__ void relative_velocity3(const float g[19], int64_t i,
     }
 }
 
+// Rows of the 3x3 (y, z) neighbourhood of row (y, z): offsets of rows (y + dy, z + dz),
+// periodic.
+struct Rows3 {
+    int64_t r00, rm0, rp0, r0m, r0p, rmm, rpp, rmp, rpm;
+    __device__ __forceinline__ Rows3(int y, int z, int nx, int ny, int nz) {
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+        auto row = [&](int yy, int zz) { return ((int64_t)zz * ny + yy) * nx; };
+        r00 = row(y, z), rm0 = row(ym, z), rp0 = row(yp, z);
+        r0m = row(y, zm), r0p = row(y, zp);
+        rmm = row(ym, zm), rpp = row(yp, zp), rmp = row(ym, zp), rpm = row(yp, zm);
+    }
+};
+
+// Thread blocks of 32 to kThreads3 threads (a multiple of 32) along one row, each thread
+// owning NV consecutive nodes, sized to the row so that short rows leave no warp idle; the
+// row index stays uniform across the block (its offsets are computed once per warp, in
+// uniform registers).
+//
 // One thread: NV consecutive nodes of the row (y, z). Population j is pulled from
 // (x, y, z) - c_j, periodic (relation (transport)).
 template <typename T, int NV, int UM>
@@ -41,34 +68,29 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
     const int64_t n = (int64_t)nx * ny * nz;
     const PackLane p = pack_lane<NV>(nx);
     for (int z = blockIdx.z; z < nz; z += gridDim.z) {
-        const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
         for (int y = blockIdx.y; y < ny; y += gridDim.y) {
-            const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-            auto row = [&](int yy, int zz) { return ((int64_t)zz * ny + yy) * nx; };
-            const int64_t r00 = row(y, z), rm0 = row(ym, z), rp0 = row(yp, z);
-            const int64_t r0m = row(y, zm), r0p = row(y, zp);
-            const int64_t rmm = row(ym, zm), rpp = row(yp, zp), rmp = row(ym, zp), rpm = row(yp, zm);
+            const Rows3 r(y, z, nx, ny, nz);
             float g[19][NV];
             const T* s = src;
-            load_pack<T, NV>(s + r00 + p.x0, p.act, g[0]);
-            load_from_left<T, NV>(s + 1 * n + r00, p.x0, p.xprev, p.act, p.left_edge, g[1]);
-            load_from_right<T, NV>(s + 2 * n + r00, p.x0, p.xnext, p.act, p.right_edge, g[2]);
-            load_pack<T, NV>(s + 3 * n + rm0 + p.x0, p.act, g[3]);
-            load_pack<T, NV>(s + 4 * n + rp0 + p.x0, p.act, g[4]);
-            load_pack<T, NV>(s + 5 * n + r0m + p.x0, p.act, g[5]);
-            load_pack<T, NV>(s + 6 * n + r0p + p.x0, p.act, g[6]);
-            load_from_left<T, NV>(s + 7 * n + rm0, p.x0, p.xprev, p.act, p.left_edge, g[7]);
-            load_from_right<T, NV>(s + 8 * n + rp0, p.x0, p.xnext, p.act, p.right_edge, g[8]);
-            load_from_left<T, NV>(s + 9 * n + rp0, p.x0, p.xprev, p.act, p.left_edge, g[9]);
-            load_from_right<T, NV>(s + 10 * n + rm0, p.x0, p.xnext, p.act, p.right_edge, g[10]);
-            load_from_left<T, NV>(s + 11 * n + r0m, p.x0, p.xprev, p.act, p.left_edge, g[11]);
-            load_from_right<T, NV>(s + 12 * n + r0p, p.x0, p.xnext, p.act, p.right_edge, g[12]);
-            load_from_left<T, NV>(s + 13 * n + r0p, p.x0, p.xprev, p.act, p.left_edge, g[13]);
-            load_from_right<T, NV>(s + 14 * n + r0m, p.x0, p.xnext, p.act, p.right_edge, g[14]);
-            load_pack<T, NV>(s + 15 * n + rmm + p.x0, p.act, g[15]);
-            load_pack<T, NV>(s + 16 * n + rpp + p.x0, p.act, g[16]);
-            load_pack<T, NV>(s + 17 * n + rmp + p.x0, p.act, g[17]);
-            load_pack<T, NV>(s + 18 * n + rpm + p.x0, p.act, g[18]);
+            load_pack<T, NV>(s + r.r00 + p.x0, p.act, g[0]);
+            load_from_left<T, NV>(s + 1 * n + r.r00, p.x0, p.xprev, p.act, p.left_edge, g[1]);
+            load_from_right<T, NV>(s + 2 * n + r.r00, p.x0, p.xnext, p.act, p.right_edge, g[2]);
+            load_pack<T, NV>(s + 3 * n + r.rm0 + p.x0, p.act, g[3]);
+            load_pack<T, NV>(s + 4 * n + r.rp0 + p.x0, p.act, g[4]);
+            load_pack<T, NV>(s + 5 * n + r.r0m + p.x0, p.act, g[5]);
+            load_pack<T, NV>(s + 6 * n + r.r0p + p.x0, p.act, g[6]);
+            load_from_left<T, NV>(s + 7 * n + r.rm0, p.x0, p.xprev, p.act, p.left_edge, g[7]);
+            load_from_right<T, NV>(s + 8 * n + r.rp0, p.x0, p.xnext, p.act, p.right_edge, g[8]);
+            load_from_left<T, NV>(s + 9 * n + r.rp0, p.x0, p.xprev, p.act, p.left_edge, g[9]);
+            load_from_right<T, NV>(s + 10 * n + r.rm0, p.x0, p.xnext, p.act, p.right_edge, g[10]);
+            load_from_left<T, NV>(s + 11 * n + r.r0m, p.x0, p.xprev, p.act, p.left_edge, g[11]);
+            load_from_right<T, NV>(s + 12 * n + r.r0p, p.x0, p.xnext, p.act, p.right_edge, g[12]);
+            load_from_left<T, NV>(s + 13 * n + r.r0p, p.x0, p.xprev, p.act, p.left_edge, g[13]);
+            load_from_right<T, NV>(s + 14 * n + r.r0m, p.x0, p.xnext, p.act, p.right_edge, g[14]);
+            load_pack<T, NV>(s + 15 * n + r.rmm + p.x0, p.act, g[15]);
+            load_pack<T, NV>(s + 16 * n + r.rpp + p.x0, p.act, g[16]);
+            load_pack<T, NV>(s + 17 * n + r.rmp + p.x0, p.act, g[17]);
+            load_pack<T, NV>(s + 18 * n + r.rpm + p.x0, p.act, g[18]);
             if (p.act) {
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
@@ -77,13 +99,118 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
                     for (int j = 0; j < 19; ++j) h[j] = g[j][k];
                     float ux = 0.0f, uy = 0.0f, uz = 0.0f;
                     if constexpr (UM != UM_ZERO && UM != UM_FLUID)
-                        relative_velocity3<UM>(h, r00 + p.x0 + k, n, a, ux, uy, uz);
+                        relative_velocity3<UM>(h, r.r00 + p.x0 + k, n, a, ux, uy, uz);
                     relax_node3<UM>(h, ux, uy, uz, a.s, a.ref);
 #pragma unroll
                     for (int j = 0; j < 19; ++j) g[j][k] = h[j];
                 }
 #pragma unroll
-                for (int j = 0; j < 19; ++j) store_pack<T, NV>(dst + j * n + r00 + p.x0, g[j]);
+                for (int j = 0; j < 19; ++j) store_pack<T, NV>(dst + j * n + r.r00 + p.x0, g[j]);
+            }
+        }
+    }
+}
+
+// The same step for 16-bit storage with the packs held in storage form (two values per
+// register): wider packs (fewer, larger memory accesses and less per-node address and halo
+// work) at the register cost of narrow ones. PAIRS: 0 relaxes node by node, converting
+// each value on its own; 1 converts a node pair at once and relaxes its two nodes; 2
+// relaxes the pair by packed FP32 instructions (F2). Registers are capped at 128 per
+// thread (four 128-thread blocks per SM). Blocks span several rows when a row has fewer
+// than 128 packs (a warp stays within one row); with the row index per thread the
+// compiler spills less than with one row per block (measured).
+template <typename T, int NV, int UM, int PAIRS, int RCP>
+__global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict__ src,
+                                                         T* __restrict__ dst, StepArgs3 a) {
+    static_assert(sizeof(T) == 2 && NV >= 4 && NV % 2 == 0, "16-bit packs of 4 or more");
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int64_t n = (int64_t)nx * ny * nz;
+    const PackLane p = pack_lane<NV>(nx);
+    for (int z = blockIdx.z; z < nz; z += gridDim.z) {
+        for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < ny; y += gridDim.y * blockDim.y) {
+            const Rows3 r(y, z, nx, ny, nz);
+            uint32_t w[19][NV / 2];
+            const T* s = src;
+            load_raw16<NV>(s + r.r00 + p.x0, p.act, w[0]);
+            load_raw16_from_left<T, NV>(s + 1 * n + r.r00, p.x0, p.xprev, p.act, p.left_edge, w[1]);
+            load_raw16_from_right<T, NV>(s + 2 * n + r.r00, p.x0, p.xnext, p.act, p.right_edge, w[2]);
+            load_raw16<NV>(s + 3 * n + r.rm0 + p.x0, p.act, w[3]);
+            load_raw16<NV>(s + 4 * n + r.rp0 + p.x0, p.act, w[4]);
+            load_raw16<NV>(s + 5 * n + r.r0m + p.x0, p.act, w[5]);
+            load_raw16<NV>(s + 6 * n + r.r0p + p.x0, p.act, w[6]);
+            load_raw16_from_left<T, NV>(s + 7 * n + r.rm0, p.x0, p.xprev, p.act, p.left_edge, w[7]);
+            load_raw16_from_right<T, NV>(s + 8 * n + r.rp0, p.x0, p.xnext, p.act, p.right_edge, w[8]);
+            load_raw16_from_left<T, NV>(s + 9 * n + r.rp0, p.x0, p.xprev, p.act, p.left_edge, w[9]);
+            load_raw16_from_right<T, NV>(s + 10 * n + r.rm0, p.x0, p.xnext, p.act, p.right_edge, w[10]);
+            load_raw16_from_left<T, NV>(s + 11 * n + r.r0m, p.x0, p.xprev, p.act, p.left_edge, w[11]);
+            load_raw16_from_right<T, NV>(s + 12 * n + r.r0p, p.x0, p.xnext, p.act, p.right_edge, w[12]);
+            load_raw16_from_left<T, NV>(s + 13 * n + r.r0p, p.x0, p.xprev, p.act, p.left_edge, w[13]);
+            load_raw16_from_right<T, NV>(s + 14 * n + r.r0m, p.x0, p.xnext, p.act, p.right_edge, w[14]);
+            load_raw16<NV>(s + 15 * n + r.rmm + p.x0, p.act, w[15]);
+            load_raw16<NV>(s + 16 * n + r.rpp + p.x0, p.act, w[16]);
+            load_raw16<NV>(s + 17 * n + r.rmp + p.x0, p.act, w[17]);
+            load_raw16<NV>(s + 18 * n + r.rpm + p.x0, p.act, w[18]);
+            if (p.act && PAIRS == 0) {
+#pragma unroll
+                for (int e = 0; e < NV; ++e) {
+                    float h[19];
+#pragma unroll
+                    for (int j = 0; j < 19; ++j) h[j] = Cvt16<T>::get(w[j][e / 2], e % 2);
+                    float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+                    if constexpr (UM != UM_ZERO && UM != UM_FLUID)
+                        relative_velocity3<UM>(h, r.r00 + p.x0 + e, n, a, ux, uy, uz);
+                    relax_node3<UM, RCP>(h, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                    for (int j = 0; j < 19; ++j) w[j][e / 2] = Cvt16<T>::put(w[j][e / 2], e % 2, h[j]);
+                }
+            } else if (p.act) {
+#pragma unroll
+                for (int k = 0; k < NV / 2; ++k) {
+                    const int64_t i = r.r00 + p.x0 + 2 * k;  // first node of the pair
+                    if constexpr (PAIRS == 2) {
+                        F2 h[19];
+#pragma unroll
+                        for (int j = 0; j < 19; ++j) {
+                            const float2 f = Cvt16<T>::unpack(w[j][k]);
+                            h[j] = pack2(f.x, f.y);
+                        }
+                        F2 ux(0.0f), uy(0.0f), uz(0.0f);
+                        if constexpr (UM != UM_ZERO && UM != UM_FLUID) {
+                            const F2 amp(a.amp_t);
+                            ux = amp * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
+                            uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
+                            uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
+                        }
+                        relax_node3<UM, RCP>(h, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                        for (int j = 0; j < 19; ++j) {
+                            float lo, hi;
+                            unpack2(h[j], lo, hi);
+                            w[j][k] = Cvt16<T>::pack(lo, hi);
+                        }
+                    } else {
+                        float h0[19], h1[19];
+#pragma unroll
+                        for (int j = 0; j < 19; ++j) {
+                            const float2 f = Cvt16<T>::unpack(w[j][k]);
+                            h0[j] = f.x;
+                            h1[j] = f.y;
+                        }
+                        float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+                        if constexpr (UM != UM_ZERO && UM != UM_FLUID)
+                            relative_velocity3<UM>(h0, i, n, a, ux, uy, uz);
+                        relax_node3<UM, RCP>(h0, ux, uy, uz, a.s, a.ref);
+                        if constexpr (UM != UM_ZERO && UM != UM_FLUID)
+                            relative_velocity3<UM>(h1, i + 1, n, a, ux, uy, uz);
+                        relax_node3<UM, RCP>(h1, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                        for (int j = 0; j < 19; ++j) w[j][k] = Cvt16<T>::pack(h0[j], h1[j]);
+                    }
+                }
+            }
+            if (p.act) {
+#pragma unroll
+                for (int j = 0; j < 19; ++j) store_raw16<NV>(dst + j * n + r.r00 + p.x0, w[j]);
             }
         }
     }
@@ -216,27 +343,46 @@ int grid1d3(int64_t n) {
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+// Block shape for NV-node packs on rows of nx nodes: 32 to kThreads3 threads along x (a
+// multiple of 32), and, for kernels that take it, the rest of the block on further rows.
+inline dim3 step3_block(int nx, int nv, bool multi_row) {
+    const int packs = (nx + nv - 1) / nv;
+    int tx = ((packs + 31) / 32) * 32;
+    if (tx > kThreads3) tx = kThreads3;
+    return dim3(tx, multi_row ? kThreads3 / tx : 1, 1);
+}
+
+template <typename K>
+cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                    int nv, bool multi_row = false) {
+    const dim3 b = step3_block(a.nx, nv, multi_row);
+    const int packs = (a.nx + nv - 1) / nv;
+    const int gy = (a.ny + (int)b.y - 1) / (int)b.y;
+    const dim3 grid((packs + b.x - 1) / b.x, gy < 65535 ? gy : 65535, a.nz < 65535 ? a.nz : 65535);
+    using TT = typename KernelArg<K>::type;
+    kernel<<<grid, b, 0, st>>>(static_cast<const TT*>(src), static_cast<TT*>(dst), a);
+    return cudaGetLastError();
+}
+
+// 16-bit packs of 4 and 8 nodes run in storage form (k_step3_r16), relaxed in pairs by
+// packed FP32 instructions, with the correctly rounded 1/rho (measured fastest on GB300 at
+// 256^3: 68 k MLUPS with 8-node packs against 54 k for 2-node packs converted on load).
+constexpr int kPairs3 = 2;
+constexpr int kRcp3 = RCP_RN;
+
 template <typename T, int UM>
 cudaError_t step3_nv(const void* src, void* dst, const StepArgs3& a, cudaStream_t st, int nv) {
-    const dim3 grid = dim3(1, a.ny < 65535 ? a.ny : 65535, a.nz < 65535 ? a.nz : 65535);
-    const T* s = static_cast<const T*>(src);
-    T* d = static_cast<T*>(dst);
-    if (nv == 1) {
-        dim3 g = grid;
-        g.x = (a.nx + kThreads3 - 1) / kThreads3;
-        k_step3<T, 1, UM><<<g, kThreads3, 0, st>>>(s, d, a);
-    } else if (nv == 2) {
-        dim3 g = grid;
-        g.x = (a.nx / 2 + kThreads3 - 1) / kThreads3;
-        k_step3<T, 2, UM><<<g, kThreads3, 0, st>>>(s, d, a);
-    } else if (nv == 4) {
-        dim3 g = grid;
-        g.x = (a.nx / 4 + kThreads3 - 1) / kThreads3;
-        k_step3<T, 4, UM><<<g, kThreads3, 0, st>>>(s, d, a);
+    if constexpr (sizeof(T) == 2) {
+        if (nv == 4)
+            return launch3(k_step3_r16<T, 4, UM, kPairs3, kRcp3>, src, dst, a, st, nv, true);
+        if (nv == 8)
+            return launch3(k_step3_r16<T, 8, UM, kPairs3, kRcp3>, src, dst, a, st, nv, true);
     } else {
-        return cudaErrorInvalidValue;
+        if (nv == 4) return launch3(k_step3<T, 4, UM>, src, dst, a, st, nv);
     }
-    return cudaGetLastError();
+    if (nv == 1) return launch3(k_step3<T, 1, UM>, src, dst, a, st, nv);
+    if (nv == 2) return launch3(k_step3<T, 2, UM>, src, dst, a, st, nv);
+    return cudaErrorInvalidValue;
 }
 
 template <typename T>
@@ -253,8 +399,8 @@ cudaError_t step3_um(const void* src, void* dst, const StepArgs3& a, cudaStream_
 }  // namespace
 
 int step3_vector_width(int storage, int nx) {
-    // Measured fastest on GB300 at 256^3: 4-node packs for FP32, 2-node packs for 16-bit.
-    const int widest = storage == kStoreF32 ? 4 : 2;
+    // Measured fastest on GB300 at 256^3: 4-node packs for FP32, 8-node packs for 16-bit.
+    const int widest = storage == kStoreF32 ? 4 : 8;
     for (int nv = widest; nv > 1; nv >>= 1)
         if (nx % nv == 0) return nv;
     return 1;

@@ -204,7 +204,7 @@ int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread) {
         h->width = w;
         return LBMRV_OK;
     }
-    const int widest = h->dim == 3 ? 4 : (h->storage == LBMRV_FP32 ? 4 : 8);
+    const int widest = h->storage == LBMRV_FP32 ? 4 : 8;
     if ((w != 2 && w != 4 && w != 8) || w > widest || h->nx % w != 0)
         return fail(h, LBMRV_E_INVAL,
                     "lbmrv_set_kernel_width: %d must be 0, 1 or a pack width (<= %d) dividing nx",

@@ -8,6 +8,8 @@
 // (they shuffle with a full mask); inactive lanes (x0 >= nx) load nothing.
 #pragma once
 
+#include <cstring>
+
 #include "d2q9.cuh"
 
 namespace lbmrv {
@@ -174,6 +176,112 @@ __device__ __forceinline__ void gather_pack(const T* __restrict__ src, int64_t n
     load_from_left<T, NV>(src + 7 * n + rm, p.x0, p.xprev, p.act, p.left_edge, g[7]);
     load_from_right<T, NV>(src + 8 * n + rm, p.x0, p.xnext, p.act, p.right_edge, g[8]);
 }
+
+// ---- 16-bit packs kept in storage form: NV elements in NV/2 32-bit words, element 2i in
+// the low half of word i. The one-element shifts of the x-moving planes are byte permutes;
+// values are converted to FP32 only when a node pair is relaxed.
+template <int NV>
+struct alignas(2 * NV) Raw16 {
+    uint32_t w[NV / 2];
+};
+
+template <int NV>
+__device__ __forceinline__ void load_raw16(const void* p, bool act, uint32_t out[NV / 2]) {
+    if (act) {
+        const Raw16<NV> r = *reinterpret_cast<const Raw16<NV>*>(p);
+#pragma unroll
+        for (int i = 0; i < NV / 2; ++i) out[i] = r.w[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < NV / 2; ++i) out[i] = 0u;
+    }
+}
+
+__device__ __forceinline__ uint32_t load_elem16(const void* p) {
+    return *reinterpret_cast<const unsigned short*>(p);
+}
+
+// Elements (prev, v0, ..., v_{NV-2}) of a row, in storage form.
+template <typename T, int NV>
+__device__ __forceinline__ void load_raw16_from_left(const T* __restrict__ row, int x0, int xprev,
+                                                     bool act, bool edge, uint32_t out[NV / 2]) {
+    uint32_t v[NV / 2];
+    load_raw16<NV>(row + x0, act, v);
+    uint32_t prev = __shfl_up_sync(kFullMask, v[NV / 2 - 1], 1) >> 16;
+    if (edge && act) prev = load_elem16(row + xprev);
+    out[0] = __byte_perm(prev, v[0], 0x5410);
+#pragma unroll
+    for (int i = 1; i < NV / 2; ++i) out[i] = __byte_perm(v[i - 1], v[i], 0x5432);
+}
+
+// Elements (v1, ..., v_{NV-1}, next) of a row, in storage form.
+template <typename T, int NV>
+__device__ __forceinline__ void load_raw16_from_right(const T* __restrict__ row, int x0, int xnext,
+                                                      bool act, bool edge, uint32_t out[NV / 2]) {
+    uint32_t v[NV / 2];
+    load_raw16<NV>(row + x0, act, v);
+    uint32_t next = __shfl_down_sync(kFullMask, v[0], 1);
+    if (edge && act) next = load_elem16(row + xnext);
+#pragma unroll
+    for (int i = 0; i < NV / 2 - 1; ++i) out[i] = __byte_perm(v[i], v[i + 1], 0x5432);
+    out[NV / 2 - 1] = __byte_perm(v[NV / 2 - 1], next, 0x5432);
+}
+
+template <int NV>
+__device__ __forceinline__ void store_raw16(void* p, const uint32_t w[NV / 2]) {
+    Raw16<NV> r;
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) r.w[i] = w[i];
+    *reinterpret_cast<Raw16<NV>*>(p) = r;
+}
+
+// A word of two 16-bit values <-> two floats (low half first).
+template <typename T>
+struct Cvt16;
+
+template <>
+struct Cvt16<__half> {
+    __device__ __forceinline__ static float2 unpack(uint32_t w) {
+        __half2 h;
+        memcpy(&h, &w, 4);
+        return __half22float2(h);
+    }
+    // element `hi` (0: low half, 1: high half) of a word, and the word with it replaced
+    __device__ __forceinline__ static float get(uint32_t w, int hi) {
+        const unsigned short b = (unsigned short)(hi ? w >> 16 : w & 0xffffu);
+        return __half2float(__ushort_as_half(b));
+    }
+    __device__ __forceinline__ static uint32_t put(uint32_t w, int hi, float v) {
+        const uint32_t b = __half_as_ushort(__float2half_rn(v));
+        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+    }
+    __device__ __forceinline__ static uint32_t pack(float a, float b) {
+        const __half2 h = __floats2half2_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
+
+template <>
+struct Cvt16<__nv_bfloat16> {
+    __device__ __forceinline__ static float2 unpack(uint32_t w) {
+        return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+    }
+    __device__ __forceinline__ static float get(uint32_t w, int hi) {
+        return __uint_as_float(hi ? (w & 0xffff0000u) : (w << 16));
+    }
+    __device__ __forceinline__ static uint32_t put(uint32_t w, int hi, float v) {
+        const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        return hi ? __byte_perm(w, b, 0x5410) : __byte_perm(w, b, 0x3254);
+    }
+    __device__ __forceinline__ static uint32_t pack(float a, float b) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        uint32_t w;
+        memcpy(&w, &h, 4);
+        return w;
+    }
+};
 
 template <typename T, int NV>
 __device__ __forceinline__ void store_pack(T* __restrict__ p, const float v[NV]) {

@@ -46,6 +46,20 @@ def test_parity_small_3d_every_width(mode):
         np.testing.assert_array_equal(f, outs[0])
 
 
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed"])
+def test_16bit_3d_every_width(storage, tol, mode):
+    """Every 16-bit D3Q19 kernel against the oracle: one node per thread, 2-node packs
+    converted to FP32 on load, 4- and 8-node packs kept in storage form (two values per
+    register). 40 x 7 x 5: five 8-node packs per row (a partly idle warp; several rows per
+    block), odd ny and nz. Kernels of one family agree bit for bit."""
+    shape = (40, 7, 5)
+    outs = {w: _check(shape, mode, 20, tol=tol, seed=3, storage=storage, width=w)
+            for w in (1, 2, 4, 8)}
+    np.testing.assert_array_equal(outs[2], outs[1])
+    np.testing.assert_array_equal(outs[8], outs[4])
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (7, 3, 2), (2, 9, 1), (5, 1, 4)])
 def test_parity_degenerate_3d(shape):
     for mode in ("zero", "fluid", "prescribed"):
