@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 import lbm_inputs as inp
-from pairs import f32_fields, gpu_run, oracle_run, rel_errors
+from pairs import f32_fields, gpu_run, oracle_run, reference_populations, rel_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -110,3 +110,39 @@ def test_16bit_every_kernel_width(storage, tol, mode):
         e = rel_errors(f_g, m_g, f_o, m_o)
         assert e[1] <= tol, (w, e)
         assert e[0] <= tol, (w, e)
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_full_size_8192_sampled_parity(storage):
+    """The 8192^2 precision workload in the benchmark's launch configuration (8-node packs
+    relaxed in pairs, reference form): nodes at the corners, wrap edges, pack and warp
+    boundaries and random places against the oracle on their dependency windows."""
+    import torch
+
+    import oracle
+    from paper_1312_3297_gb300 import D2Q9
+
+    L, steps = 8192, 4
+    rho, ux, uy = f32_fields(inp.perturbed_uniform(L, L, seed=0, U=U_MEAN))
+    sim = D2Q9(L, L, S, mode="fluid", storage=storage, u_ref=U_MEAN)
+    sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+    sim.step(steps)
+    g = sim.state()
+    fref = reference_populations(sim.rho_ref, U_MEAN, 1.0)
+    R = steps + 1
+    rng = np.random.default_rng(2)
+    centers = [(0, 0), (L - 1, L - 1), (0, L - 1), (L - 1, 0), (7, 3), (8, 3), (1023, 77),
+               (1024, 78), (L - 8, 5), (L - 9, L - 2)]
+    centers += [tuple(int(v) for v in rng.integers(0, L, 2)) for _ in range(6)]
+    errs, fmax = [], 0.0
+    for cx, cy in centers:
+        xs = (cx + np.arange(-R, R + 1)) % L
+        ys = (cy + np.arange(-R, R + 1)) % L
+        f0 = oracle.init_equilibrium(rho[np.ix_(ys, xs)], ux[np.ix_(ys, xs)],
+                                     uy[np.ix_(ys, xs)], 1.0)
+        ref = oracle.post_collision_state(f0, 1.0, np.asarray(S, float), 1, steps)[:, R, R]
+        got = g[:, cy, cx].double().cpu().numpy() + fref
+        errs.append(float(np.abs(got - ref).max()))
+        fmax = max(fmax, float(np.abs(ref).max()))
+    sim.close()
+    assert max(errs) <= (1e-4 if storage == "fp16" else 1e-3) * fmax, errs
