@@ -69,8 +69,9 @@ LBMRV_HD NodeMoments3 node_moments3(const float g[19]) {
 // The relaxation, in place on the deviations g of one node (R = float) or of two nodes
 // (R = F2, one per lane), for u = u~ / lambda. UM = UM_FLUID takes u~ = q / rho of the
 // state being relaxed (ux, uy, uz are outputs then); UM = UM_ZERO is the fixed-frame scheme.
-// RCP: the form of 1/rho (see recip).
-template <int UM, int RCP = RCP_RN, typename R>
+// RCP: the form of 1/rho (see recip). INCR = true leaves the increment g* - g in g instead
+// of g* (the caller adds it to the input, which it need not keep in registers meanwhile).
+template <int UM, int RCP = RCP_RN, bool INCR = false, typename R>
 LBMRV_HD void relax_node3(R g[19], R& ux, R& uy, R& uz, const Rates3& s,
                           const StoreRef3& ref) {
     // Sums and differences of opposite populations.
@@ -180,35 +181,35 @@ LBMRV_HD void relax_node3(R g[19], R& ux, R& uy, R& uz, const Rates3& s,
     const R q4 = R(-0.25f), q2 = R(-0.5f);
     {
         const R p = h_xxyy + r_xy, q = h_xxyy - r_xy, o1 = h_xyy + h_yxx, o2 = h_xyy - h_yxx;
-        g[7] = fma_(q4, p + o1, g[7]);
-        g[8] = fma_(q4, p - o1, g[8]);
-        g[9] = fma_(q4, q + o2, g[9]);
-        g[10] = fma_(q4, q - o2, g[10]);
+        g[7] = INCR ? q4 * (p + o1) : fma_(q4, p + o1, g[7]);
+        g[8] = INCR ? q4 * (p - o1) : fma_(q4, p - o1, g[8]);
+        g[9] = INCR ? q4 * (q + o2) : fma_(q4, q + o2, g[9]);
+        g[10] = INCR ? q4 * (q - o2) : fma_(q4, q - o2, g[10]);
     }
     {
         const R p = h_xxzz + r_xz, q = h_xxzz - r_xz, o1 = h_xzz + h_zxx, o2 = h_xzz - h_zxx;
-        g[11] = fma_(q4, p + o1, g[11]);
-        g[12] = fma_(q4, p - o1, g[12]);
-        g[13] = fma_(q4, q + o2, g[13]);
-        g[14] = fma_(q4, q - o2, g[14]);
+        g[11] = INCR ? q4 * (p + o1) : fma_(q4, p + o1, g[11]);
+        g[12] = INCR ? q4 * (p - o1) : fma_(q4, p - o1, g[12]);
+        g[13] = INCR ? q4 * (q + o2) : fma_(q4, q + o2, g[13]);
+        g[14] = INCR ? q4 * (q - o2) : fma_(q4, q - o2, g[14]);
     }
     {
         const R p = h_yyzz + r_yz, q = h_yyzz - r_yz, o1 = h_yzz + h_zyy, o2 = h_yzz - h_zyy;
-        g[15] = fma_(q4, p + o1, g[15]);
-        g[16] = fma_(q4, p - o1, g[16]);
-        g[17] = fma_(q4, q + o2, g[17]);
-        g[18] = fma_(q4, q - o2, g[18]);
+        g[15] = INCR ? q4 * (p + o1) : fma_(q4, p + o1, g[15]);
+        g[16] = INCR ? q4 * (p - o1) : fma_(q4, p - o1, g[16]);
+        g[17] = INCR ? q4 * (q + o2) : fma_(q4, q + o2, g[17]);
+        g[18] = INCR ? q4 * (q - o2) : fma_(q4, q - o2, g[18]);
     }
     const R sx = r_xx - (h_xxyy + h_xxzz), sy = r_yy - (h_xxyy + h_yyzz);
     const R sz = r_zz - (h_xxzz + h_yyzz);
     const R mx = h_xyy + h_xzz, my = h_yxx + h_yzz, mz = h_zxx + h_zyy;
-    g[1] = fma_(q2, sx - mx, g[1]);
-    g[2] = fma_(q2, sx + mx, g[2]);
-    g[3] = fma_(q2, sy - my, g[3]);
-    g[4] = fma_(q2, sy + my, g[4]);
-    g[5] = fma_(q2, sz - mz, g[5]);
-    g[6] = fma_(q2, sz + mz, g[6]);
-    g[0] = g[0] - (((h_xxyy + h_xxzz) + h_yyzz) - rt);
+    g[1] = INCR ? q2 * (sx - mx) : fma_(q2, sx - mx, g[1]);
+    g[2] = INCR ? q2 * (sx + mx) : fma_(q2, sx + mx, g[2]);
+    g[3] = INCR ? q2 * (sy - my) : fma_(q2, sy - my, g[3]);
+    g[4] = INCR ? q2 * (sy + my) : fma_(q2, sy + my, g[4]);
+    g[5] = INCR ? q2 * (sz - mz) : fma_(q2, sz - mz, g[5]);
+    g[6] = INCR ? q2 * (sz + mz) : fma_(q2, sz + mz, g[6]);
+    g[0] = INCR ? rt - ((h_xxyy + h_xxzz) + h_yyzz) : g[0] - (((h_xxyy + h_xxzz) + h_yyzz) - rt);
 }
 
 }  // namespace lbmrv

@@ -115,8 +115,9 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
 // register): wider packs (fewer, larger memory accesses and less per-node address and halo
 // work) at the register cost of narrow ones. PAIRS: 0 relaxes node by node, converting
 // each value on its own; 1 converts a node pair at once and relaxes its two nodes; 2
-// relaxes the pair by packed FP32 instructions (F2). Registers are capped at 128 per
-// thread (four 128-thread blocks per SM). Blocks span several rows when a row has fewer
+// relaxes the pair by packed FP32 instructions (F2), as an increment added to the pair
+// re-read from its packed word. Registers are capped at 128 per thread (four 128-thread
+// blocks per SM). Blocks span several rows when a row has fewer
 // than 128 packs (a warp stays within one row); with the row index per thread the
 // compiler spills less than with one row per block (measured).
 template <typename T, int NV, int UM, int PAIRS, int RCP>
@@ -181,11 +182,16 @@ __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict_
                             uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
                             uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
                         }
-                        relax_node3<UM, RCP>(h, ux, uy, uz, a.s, a.ref);
+                        relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
 #pragma unroll
                         for (int j = 0; j < 19; ++j) {
+                            // re-read the stored pair: the opaque copy keeps the compiler from
+                            // holding the unpacked inputs in registers through the relaxation
+                            uint32_t wj;
+                            asm volatile("mov.b32 %0, %1;" : "=r"(wj) : "r"(w[j][k]));
+                            const float2 f = Cvt16<T>::unpack(wj);
                             float lo, hi;
-                            unpack2(h[j], lo, hi);
+                            unpack2(pack2(f.x, f.y) + h[j], lo, hi);
                             w[j][k] = Cvt16<T>::pack(lo, hi);
                         }
                     } else {
@@ -366,7 +372,7 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 
 // 16-bit packs of 4 and 8 nodes run in storage form (k_step3_r16), relaxed in pairs by
 // packed FP32 instructions, with the correctly rounded 1/rho (measured fastest on GB300 at
-// 256^3: 68 k MLUPS with 8-node packs against 54 k for 2-node packs converted on load).
+// 256^3: 70 k MLUPS with 8-node packs against 54 k for 2-node packs converted on load).
 constexpr int kPairs3 = 2;
 constexpr int kRcp3 = RCP_RN;
 
