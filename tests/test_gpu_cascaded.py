@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import lbm_inputs as inp
-from pairs import f32_fields, gpu_run, oracle_run, rel_errors
+from pairs import f32_fields, gpu_run, oracle_run, product_populations, rel_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -71,3 +71,37 @@ def test_cascaded_full_size_conservation():
     assert abs(c1[0] - c0[0]) / c0[0] < 1e-9
     assert abs(c1[1] - c0[1]) < 1e-6 * c0[0] * 0.04
     sim.close()
+
+
+def test_cascaded_full_size_sampled_parity():
+    """The cascaded workload the benchmark times (4096^2 Taylor-Green, u~ = q/rho, 4-node
+    packs): sampled nodes against Appendix B's cascade on their dependency windows."""
+    import torch
+
+    import oracle
+    from paper_1312_3297_gb300 import D2Q9Cascaded
+
+    L, steps = 4096, 4
+    rho, ux, uy = f32_fields(inp.taylor_green(L, L, u0=0.04))
+    sim = D2Q9Cascaded(L, L, SG, mode="fluid")
+    sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+    sim.step(steps)
+    g = sim.state()
+    fref = product_populations(sim.rho_ref, (0.0, 0.0), 1.0)
+    R = steps + 1
+    rng = np.random.default_rng(4)
+    centers = [(0, 0), (L - 1, L - 1), (3, L - 1), (4, 0), (511, 2048), (512, 2049)]
+    centers += [tuple(int(v) for v in rng.integers(0, L, 2)) for _ in range(6)]
+    errs, fmax = [], 0.0
+    for cx, cy in centers:
+        xs = (cx + np.arange(-R, R + 1)) % L
+        ys = (cy + np.arange(-R, R + 1)) % L
+        f0 = oracle.init_equilibrium_product(rho[np.ix_(ys, xs)], ux[np.ix_(ys, xs)],
+                                             uy[np.ix_(ys, xs)], 1.0)
+        ref = oracle.post_collision_state(f0, 1.0, np.asarray(SG, float), 1, steps,
+                                          method=CASCADED)[:, R, R]
+        got = g[:, cy, cx].double().cpu().numpy() + fref
+        errs.append(float(np.abs(got - ref).max()))
+        fmax = max(fmax, float(np.abs(ref).max()))
+    sim.close()
+    assert max(errs) <= TOL * fmax, errs

@@ -80,10 +80,16 @@ def test_reduced_precision_3d(storage):
     assert e[1] <= (2e-3 if storage == "fp16" else 2e-2), e
 
 
-def test_full_size_256_sampled_parity_and_conservation():
+@pytest.mark.parametrize("storage,tol,mass_tol,mom_tol", [
+    ("fp32", TOL, 1e-9, 1e-6),
+    ("fp16", 2e-4, 1e-5, 1e-3),
+    ("bf16", 3e-3, 1e-4, 1e-2),
+])
+def test_full_size_256_sampled_parity_and_conservation(storage, tol, mass_tol, mom_tol):
     """3D Taylor-Green vortex u0 = 0.04 on 256^3 (u~ = q/rho, s_nu = 1.7) in the benchmark's
-    launch configuration: sampled nodes against the oracle on their dependency cone, and
-    mass / momentum over 100 steps."""
+    launch configuration (FP32: 4-node packs; 16-bit: 8-node packs in storage form): sampled
+    nodes against the oracle on their dependency cone, and mass / momentum over 100 steps
+    (16-bit storage rounding bounds their drift)."""
     import torch
 
     from oracle import d3q19 as o3
@@ -92,14 +98,15 @@ def test_full_size_256_sampled_parity_and_conservation():
     L, steps = 256, 4
     d = inp.taylor_green_3d(L, L, L, u0=0.04)
     rho, u = inp.to_f32_exact(d["rho"]), inp.to_f32_exact(d["u"])
-    sim = D3Q19(L, L, L, S3, mode="fluid")
+    sim = D3Q19(L, L, L, S3, mode="fluid", storage=storage)
     sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in u))
     c0 = sim.conserved3()
     sim.step(steps)
     g = sim.state()
     fref = reference_populations3(sim.rho_ref, (0, 0, 0))
     rng = np.random.default_rng(1)
-    centers = [(0, 0, 0), (L - 1, L - 1, L - 1), (1, 0, L - 1), (127, 128, 5)]
+    centers = [(0, 0, 0), (L - 1, L - 1, L - 1), (1, 0, L - 1), (127, 128, 5), (7, 3, 250),
+               (8, 4, 251), (L - 8, 200, 0), (L - 9, 0, 17)]
     centers += [tuple(int(v) for v in rng.integers(0, L, 3)) for _ in range(4)]
     R = steps + 1
     errs, fmax = [], 0.0
@@ -115,10 +122,10 @@ def test_full_size_256_sampled_parity_and_conservation():
         got = g[:, cz, cy, cx].double().cpu().numpy() + fref
         errs.append(np.abs(got - ref).max())
         fmax = max(fmax, np.abs(ref).max())
-    assert max(errs) / fmax <= TOL, errs
+    assert max(errs) / fmax <= tol, errs
     sim.step(96)
     c1 = sim.conserved3()
-    assert abs(c1[0] - c0[0]) / c0[0] < 1e-9
+    assert abs(c1[0] - c0[0]) / c0[0] < mass_tol
     for a in (1, 2, 3):
-        assert abs(c1[a] - c0[a]) < 1e-6 * c0[0] * 0.04
+        assert abs(c1[a] - c0[a]) < mom_tol * c0[0] * 0.04
     sim.close()
