@@ -77,18 +77,29 @@ int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
     if (rc != LBMRV_OK) return rc;
     DeviceGuard g(h->device);
     const size_t bytes = (size_t)(9 * h->n) * sizeof(float);
-    const int nv = choose_width(h, h->f[0], h->f[1]);
+    // the pack width must suit both the handle's buffers and the checkpoint slots
+    const int nv_f = choose_width(h, h->f[0], h->f[1]), nv_w = choose_width(h, ws_dev, ws_dev);
+    const int nv = nv_f < nv_w ? nv_f : nv_w;
     const int64_t t0 = h->t;
     cudaError_t e = cudaMemcpyAsync(at(ws_dev, 0), h->f[h->cur], bytes, cudaMemcpyDeviceToDevice,
                                     h->stream);
+    // Checkpointed states are written by their step straight into their slot (no copy); the
+    // next step reads them there. The final state ends in the handle's buffers.
+    const void* src = h->f[h->cur];
+    int cur = h->cur;
     for (int64_t k = 1; k <= n && e == cudaSuccess; ++k) {
-        e = launch_handle_step(h, nv, h->f[h->cur], h->f[1 - h->cur], t0 + k);
-        h->cur = 1 - h->cur;
+        void* dst;
+        if (k % seg == 0 && k < n)
+            dst = at(ws_dev, (size_t)(k / seg) * L.state);
+        else
+            dst = src == h->f[cur] ? h->f[1 - cur] : h->f[cur];
+        e = launch_handle_step(h, nv, src, dst, t0 + k);
+        if (dst == h->f[0]) cur = 0;
+        if (dst == h->f[1]) cur = 1;
+        src = dst;
         h->t = t0 + k;
-        if (e == cudaSuccess && k % seg == 0 && k < n)
-            e = cudaMemcpyAsync(at(ws_dev, (size_t)(k / seg) * L.state), h->f[h->cur], bytes,
-                                cudaMemcpyDeviceToDevice, h->stream);
     }
+    h->cur = cur;
     if (e != cudaSuccess) {
         h->ckpt_valid = false;
         return cuda_fail(h, e, "lbmrv_forward_checkpointed");
