@@ -20,13 +20,13 @@ namespace lbmrv {
 
 namespace {
 
-// Prescribed base field u~0 at node (x, y): analytic (cos 2pi y/ny, sin 2pi x/nx) or a
-// caller field [2][n].
+// Prescribed base field u~0 at node (x, y): analytic (cos 2pi y/ny, sin 2pi x/nx; the
+// row's cosine cy is computed once per row by the caller) or a caller field [2][n].
 template <int UM>
-__device__ __forceinline__ void base_field(int x, int y, int64_t i, const StepArgs& a,
+__device__ __forceinline__ void base_field(int x, float cy, int64_t i, const StepArgs& a,
                                            float& bx, float& by) {
     if (UM == UM_ANALYTIC) {
-        bx = cospif(a.two_over_ny * (float)y);
+        bx = cy;
         by = __ldg(a.sin_x + x);
     } else if (UM == UM_FIELD) {
         const int64_t n = (int64_t)a.nx * a.ny;
@@ -89,6 +89,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __res
             for (int j = 0; j < 9; ++j) load_pack<float, NV>(a_in + j * n + r0 + p.x0, p.act, adj[j]);
         }
         if (p.act) {
+            const float cy = UM == UM_ANALYTIC ? cospif(a.two_over_ny * (float)y) : 0.0f;
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
                 float h[9], ah[9], o[9];
@@ -100,7 +101,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __res
                 const int x = p.x0 + k;
                 const int64_t i = r0 + x;
                 float bx, by, ux, uy;
-                base_field<UM>(x, y, i, a, bx, by);
+                base_field<UM>(x, cy, i, a, bx, by);
                 if (UM == UM_FLUID) {
                     const NodeMoments m = node_moments(h);
                     const float ir = recip(a.ref.rho + m.drho);

@@ -176,3 +176,51 @@ def test_adjoint_with_reference_velocity_storage():
     assert abs(a[0] - b[0]) <= 1e-6 * abs(a[0])
     assert _rel(b[1], a[1]) <= 1e-4
     assert abs(b[2][4] + b[2][5] - a[2][4] - a[2][5]) <= 1e-4 * abs(a[2][4] + a[2][5])
+
+
+@pytest.mark.parametrize("mode", ["fluid", "prescribed"])
+def test_velocity_probe_misfit_through_autograd(mode):
+    """A velocity-probe misfit L = 1/2 sum_p |u(x_p) - u_p|^2 of the final state, through
+    the torch.autograd.Function: gradients with respect to u0, s_nu and the amplitude A of
+    the prescribed u~ against FP64 reverse mode of the torch statement of the scheme."""
+    import torch
+
+    import oracle.torch_ref as tr
+    from paper_1312_3297_gb300 import D2Q9
+    from paper_1312_3297_gb300.autograd import Rollout
+
+    nx, ny, steps = 48, 40, 40
+    rho, ux, uy = f32_fields(inp.noisy_shear_wave(nx, ny, seed=8))
+    rng = np.random.default_rng(9)
+    px, py = rng.integers(0, nx, 12), rng.integers(0, ny, 12)
+    target = 0.02 * rng.standard_normal((2, 12))
+    mid = {"fluid": 1, "prescribed": 2}[mode]
+
+    # FP64 reference
+    u0r = torch.tensor(np.stack([ux, uy]), dtype=torch.float64, requires_grad=True)
+    snr = torch.tensor(1.9, dtype=torch.float64, requires_grad=True)
+    ampr = torch.tensor(0.03, dtype=torch.float64, requires_grad=True)
+    f = tr.final_state(torch.as_tensor(rho, dtype=torch.float64), u0r, 1.0, tr.rates(S, snr),
+                       mid, steps, tr.analytic_base_field(nx, ny), ampr, 1000.0)
+    r_, qx, qy = tr.moments(f, 1.0)
+    u_probe = torch.stack([qx / r_, qy / r_])[:, py, px]
+    Lr = 0.5 * ((u_probe - torch.as_tensor(target)) ** 2).sum()
+    gu, gs, ga = torch.autograd.grad(Lr, (u0r, snr, ampr), allow_unused=True)
+
+    # GPU through the autograd.Function
+    sim = D2Q9(nx, ny, S, mode=mode)
+    sim.set_utilde(None, 0.03, 1000.0)
+    u0 = torch.tensor(np.stack([ux, uy]), dtype=torch.float32, device="cuda", requires_grad=True)
+    s_nu = torch.tensor(1.9, dtype=torch.float64, requires_grad=True)
+    amp = torch.tensor(0.03, dtype=torch.float64, requires_grad=True)
+    r, u = Rollout.apply(u0, s_nu, amp, sim, steps, 7,
+                         torch.as_tensor(rho, dtype=torch.float32, device="cuda"))
+    tgt = torch.as_tensor(target, dtype=torch.float64, device="cuda")
+    L = 0.5 * ((u.double()[:, py, px] - tgt) ** 2).sum()
+    L.backward()
+    sim.close()
+    np.testing.assert_allclose(L.item(), Lr.item(), rtol=1e-5)
+    assert _rel(u0.grad.double().cpu().numpy(), gu.numpy()) <= TOL
+    assert abs(s_nu.grad.item() - gs.item()) <= TOL * abs(gs.item())
+    if mode == "prescribed":
+        assert abs(amp.grad.item() - ga.item()) <= TOL * abs(ga.item())
