@@ -112,8 +112,8 @@ LBMRV_API int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int stor
  *   lambda   velocity scale lambda > 0 (relation (lambda)).
  *   s        q relaxation rates in basis order: for D2Q9 the moment order of relation
  *            (mom): rho, q_x, q_y, e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps; for the other
- *            lattices the order of their bases above. The 1 + d conserved rates must be 0 (Section
- *            1.1); the others are finite.
+ *            lattices the order of their bases above. The 1 + d conserved rates must be 0
+ *            (Section 1.1); the others are finite.
  *   umode    LBMRV_UT_* (prescribed mode: see lbmrv_set_utilde; default A = 0).
  *   storage  LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16.
  *   rho_ref  reference density of the stored deviation g = f - w rho_ref (0 stores f).
@@ -122,7 +122,8 @@ LBMRV_API int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int stor
  *            two device buffers of lbmrv_state_bytes() each, 16-byte aligned, owned by
  *            the caller and used as the A-B pair of the pull step; or both NULL, and
  *            the library allocates (and later frees) them.
- * The handle also allocates a small reduction buffer (under 64 KB).
+ * The handle also allocates a small reduction buffer (under 64 KB) and the nx-float table
+ * sin(2 pi x / nx) of the analytic prescribed field.
  * Errors: LBMRV_E_INVAL, LBMRV_E_UNSUPPORTED, LBMRV_E_NOMEM, LBMRV_E_CUDA; *out is NULL. */
 LBMRV_API int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda,
                  const double* s, int umode, int storage, double rho_ref, void* stream,
