@@ -105,3 +105,20 @@ def test_cascaded_full_size_sampled_parity():
         fmax = max(fmax, float(np.abs(ref).max()))
     sim.close()
     assert max(errs) <= TOL * fmax, errs
+
+
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-4), ("bf16", 1.5e-3)])
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed", "field"])
+def test_cascaded_16bit_every_width(storage, tol, mode):
+    """Every 16-bit variant of the cascaded step (one node per thread, 2-, 4- and 8-node
+    packs; 8-node packs relax node pairs by packed FP32 instructions) against the oracle's
+    Geier scheme, reference form, 72 x 21 (a partly idle warp, odd ny), 40 steps."""
+    nx, ny, steps = 72, 21, 40
+    u_mean = (0.05, 0.02)
+    fields = f32_fields(inp.perturbed_uniform(nx, ny, seed=13, U=u_mean))
+    kw = dict(amp=0.03, period=50.0)
+    if mode == "field":
+        kw["ut0"] = inp.to_f32_exact(inp.prescribed_base_field(nx, ny, seed=14, smooth=False))
+    m = "prescribed" if mode == "field" else mode
+    for w in (1, 2, 4, 8):
+        _check(nx, ny, m, steps, fields, tol=tol, storage=storage, u_ref=u_mean, width=w, **kw)
