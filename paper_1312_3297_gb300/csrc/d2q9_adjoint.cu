@@ -14,6 +14,7 @@
 #include "d2q9.cuh"
 #include "d2q9_adjoint.cuh"
 #include "launch.h"
+#include "pdl.cuh"
 #include "pull.cuh"
 
 namespace lbmrv {
@@ -71,6 +72,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __res
                                                               const float* __restrict__ a_in,
                                                               float* __restrict__ mu_out,
                                                               AdjointArgs aa) {
+    pdl_wait_prior();
+    pdl_allow_next();
     const StepArgs& a = aa.step;
     const int nx = a.nx, ny = a.ny;
     const int64_t n = (int64_t)nx * ny;
@@ -295,11 +298,12 @@ template <int NV, int UM>
 cudaError_t adjoint_nv_um(const float* s_prev, const float* a_in, bool gather, float* mu_out,
                           const AdjointArgs& aa, cudaStream_t st) {
     const dim3 grid = adjoint_grid(aa.step.nx, aa.step.ny, NV);
-    if (gather)
-        k_adjoint_step<NV, UM, true><<<grid, kAdjThreads, 0, st>>>(s_prev, a_in, mu_out, aa);
-    else
-        k_adjoint_step<NV, UM, false><<<grid, kAdjThreads, 0, st>>>(s_prev, a_in, mu_out, aa);
-    return cudaGetLastError();
+    const cudaError_t e =
+        gather ? launch_pdl(k_adjoint_step<NV, UM, true>, grid, dim3(kAdjThreads), st, s_prev,
+                            a_in, mu_out, aa)
+               : launch_pdl(k_adjoint_step<NV, UM, false>, grid, dim3(kAdjThreads), st, s_prev,
+                            a_in, mu_out, aa);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int NV>

@@ -4,6 +4,7 @@
 
 #include "d2q9.cuh"
 #include "launch.h"
+#include "pdl.cuh"
 #include "pull.cuh"
 
 namespace lbmrv {
@@ -47,6 +48,8 @@ constexpr int paired_rcp() {
 template <typename T, int UM, int BASIS>
 __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
                                                      T* __restrict__ dst, StepArgs a) {
+    pdl_wait_prior();
+    pdl_allow_next();
     const int nx = a.nx, ny = a.ny;
     const int64_t n = (int64_t)nx * ny;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,6 +85,8 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 template <typename T, int NV, int UM, int BASIS>
 __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                                                   T* __restrict__ dst, StepArgs a) {
+    pdl_wait_prior();
+    pdl_allow_next();
     const int nx = a.nx, ny = a.ny;
     const int64_t n = (int64_t)nx * ny;
     const PackLane p = pack_lane<NV>(nx);
@@ -319,26 +324,28 @@ cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cuda
     const T* s = static_cast<const T*>(src);
     T* d = static_cast<T*>(dst);
     const int gy = a.ny < 65535 ? a.ny : 65535;
+    // successive steps overlap their launch with the previous step's tail (pdl.cuh)
+    cudaError_t e;
     if (nv == 1) {
-        dim3 grid((a.nx + 255) / 256, gy);
-        k_step_scalar<T, UM, BASIS><<<grid, 256, 0, st>>>(s, d, a);
+        e = launch_pdl(k_step_scalar<T, UM, BASIS>, dim3((a.nx + 255) / 256, gy), dim3(256), st,
+                       s, d, a);
     } else if (nv == 2) {
-        dim3 grid(((a.nx / 2) + 127) / 128, gy);
-        k_step_vec<T, 2, UM, BASIS><<<grid, 128, 0, st>>>(s, d, a);
+        e = launch_pdl(k_step_vec<T, 2, UM, BASIS>, dim3(((a.nx / 2) + 127) / 128, gy),
+                       dim3(128), st, s, d, a);
     } else if (nv == 4) {
-        dim3 grid(((a.nx / 4) + 127) / 128, gy);
-        k_step_vec<T, 4, UM, BASIS><<<grid, 128, 0, st>>>(s, d, a);
+        e = launch_pdl(k_step_vec<T, 4, UM, BASIS>, dim3(((a.nx / 4) + 127) / 128, gy),
+                       dim3(128), st, s, d, a);
     } else if (nv == 8) {
         if constexpr (sizeof(T) == 2) {
-            dim3 grid(((a.nx / 8) + 127) / 128, gy);
-            k_step_vec<T, 8, UM, BASIS><<<grid, 128, 0, st>>>(s, d, a);
+            e = launch_pdl(k_step_vec<T, 8, UM, BASIS>, dim3(((a.nx / 8) + 127) / 128, gy),
+                           dim3(128), st, s, d, a);
         } else {
             return cudaErrorInvalidValue;
         }
     } else {
         return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <typename T, int BASIS>

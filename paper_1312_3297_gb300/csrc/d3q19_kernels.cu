@@ -5,6 +5,7 @@
 
 #include "d3q19.cuh"
 #include "launch.h"
+#include "pdl.cuh"
 #include "pull.cuh"
 
 namespace lbmrv {
@@ -64,6 +65,8 @@ struct Rows3 {
 template <typename T, int NV, int UM>
 __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
                                                      T* __restrict__ dst, StepArgs3 a) {
+    pdl_wait_prior();
+    pdl_allow_next();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n = (int64_t)nx * ny * nz;
     const PackLane p = pack_lane<NV>(nx);
@@ -123,6 +126,8 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
 template <typename T, int NV, int UM, int PAIRS, int RCP>
 __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict__ src,
                                                          T* __restrict__ dst, StepArgs3 a) {
+    pdl_wait_prior();
+    pdl_allow_next();
     static_assert(sizeof(T) == 2 && NV >= 4 && NV % 2 == 0, "16-bit packs of 4 or more");
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n = (int64_t)nx * ny * nz;
@@ -366,8 +371,9 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
     const int gy = (a.ny + (int)b.y - 1) / (int)b.y;
     const dim3 grid((packs + b.x - 1) / b.x, gy < 65535 ? gy : 65535, a.nz < 65535 ? a.nz : 65535);
     using TT = typename KernelArg<K>::type;
-    kernel<<<grid, b, 0, st>>>(static_cast<const TT*>(src), static_cast<TT*>(dst), a);
-    return cudaGetLastError();
+    const cudaError_t e =
+        launch_pdl(kernel, grid, b, st, static_cast<const TT*>(src), static_cast<TT*>(dst), a);
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // 16-bit packs of 4 and 8 nodes run in storage form (k_step3_r16), relaxed in pairs by
