@@ -375,7 +375,7 @@ def d3q19_measure(torch, inp, steps, peak):
 def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
     """Adjoint workload: 1024^2 noisy shear wave, prescribed u~, kinetic-energy loss,
     2000 steps with sqrt(N) = 45 checkpoints. Reports the forward step, the adjoint step
-    alone (checkpoint every state on a 200-step window: no recompute), and the whole
+    alone (checkpoint every state on a 1000-step window: no recompute), and the whole
     gradient (checkpointed forward + recompute + reverse sweep + equilibrium adjoint)."""
     size = 1024
     n = size * size
@@ -390,9 +390,9 @@ def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
     # forward step alone
     sim.init_equilibrium(rho, u[0], u[1])
     sim.step(5)
-    fwd_ms = time_steps(sim, 400, torch) / 400
+    fwd_ms = time_steps(sim, 1000, torch) / 1000
     # adjoint step alone: every state checkpointed, so the sweep has no recompute
-    w = 200
+    w = 1000  # every state checkpointed: 1000 x 37.7 MB; per-call fixed work amortised
     ws = sim.adjoint_workspace(w, 1)
     sim.init_equilibrium(rho, u[0], u[1])
     sim.forward_checkpointed(w, 1, ws)
