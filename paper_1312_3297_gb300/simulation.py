@@ -65,6 +65,21 @@ class D2Q9:
         self.amp, self.period = 0.0, 0.0
         self.dtype = STORAGE_DTYPES[self.storage]
 
+    # -- stream order between torch's current stream and the handle's stream
+    def _sync_in(self):
+        """The handle's stream waits for work already queued on torch's current stream
+        (inputs that torch produced)."""
+        cur = torch.cuda.current_stream(self.device)
+        if isinstance(self.stream, torch.cuda.Stream) and cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _sync_out(self):
+        """Torch's current stream waits for the handle's queued work (outputs torch will
+        read)."""
+        cur = torch.cuda.current_stream(self.device)
+        if isinstance(self.stream, torch.cuda.Stream) and cur != self.stream:
+            cur.wait_stream(self.stream)
+
     # -- lifecycle
     def close(self):
         if getattr(self, "h", None):
@@ -98,6 +113,7 @@ class D2Q9:
             if ut0.numel() != self.DIM * self.n:
                 raise ValueError(f"u~0 must hold {self.DIM} * n values")
         self._ut0 = ut0  # keep the field alive while the handle refers to it
+        self._sync_in()
         B.lbmrv_set_utilde(self.h, ut0, amplitude, period)
 
     # -- state
@@ -108,6 +124,7 @@ class D2Q9:
         rho = torch.as_tensor(rho, dtype=torch.float32, device=self.device).contiguous()
         u = torch.stack([torch.as_tensor(c, dtype=torch.float32, device=self.device)
                          for c in u_components]).contiguous()
+        self._sync_in()
         B.lbmrv_init_equilibrium(self.h, rho, u)
         self._keep = (rho, u)  # the copy is asynchronous on the stream
 
@@ -127,6 +144,7 @@ class D2Q9:
         rho = torch.empty(self.shape, dtype=torch.float32, device=self.device)
         u = torch.empty((self.DIM,) + self.shape, dtype=torch.float32, device=self.device)
         B.lbmrv_moments(self.h, rho, u)
+        self._sync_out()
         return (rho,) + tuple(u[a] for a in range(self.DIM))
 
     def moments_host(self, rho_host=None, u_host=None):
@@ -151,12 +169,14 @@ class D2Q9:
         storage dtype."""
         out = torch.empty((self.Q,) + self.shape, dtype=self.dtype, device=self.device)
         B.lbmrv_get_state(self.h, out)
+        self._sync_out()
         return out
 
     def set_state(self, g: torch.Tensor, t: int = 0):
         g = g.to(device=self.device, dtype=self.dtype).contiguous()
         if g.numel() != self.Q * self.n:
             raise ValueError(f"state must hold {self.Q} * n values")
+        self._sync_in()
         B.lbmrv_set_state(self.h, g, t)
         self._keep = g
 
@@ -180,13 +200,17 @@ class D2Q9:
         d0 = torch.empty((9, self.ny, self.nx), dtype=torch.float32, device=self.device)
         dut = (torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
                if field_grad else None)
-        ds, da = B.lbmrv_adjoint(self.h, n, seg, ws, ws.numel(), dL_dS.contiguous(), d0, dut)
+        dL_dS = dL_dS.contiguous()
+        self._sync_in()
+        ds, da = B.lbmrv_adjoint(self.h, n, seg, ws, ws.numel(), dL_dS, d0, dut)
+        self._sync_out()
         return d0, ds, da, dut
 
     def kinetic_energy(self, grad: bool = False):
         g = (torch.empty((9, self.ny, self.nx), dtype=torch.float32, device=self.device)
              if grad else None)
         ke = B.lbmrv_kinetic_energy(self.h, g)
+        self._sync_out()
         return ke, g
 
     def moments_vjp(self, dL_drho=None, dL_du=None) -> torch.Tensor:
@@ -195,7 +219,9 @@ class D2Q9:
             dL_drho = dL_drho.to(torch.float32).contiguous()
         if dL_du is not None:
             dL_du = dL_du.to(torch.float32).contiguous()
+        self._sync_in()
         B.lbmrv_moments_vjp(self.h, dL_drho, dL_du, out)
+        self._sync_out()
         self._keep = (dL_drho, dL_du)
         return out
 
@@ -203,8 +229,12 @@ class D2Q9:
         """rho [ny, nx] or None, u [2, ny, nx] (device float32)."""
         drho = torch.empty((self.ny, self.nx), dtype=torch.float32, device=self.device)
         du = torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
-        B.lbmrv_equilibrium_vjp(self.h, None if rho is None else rho.contiguous(),
-                                u.contiguous(), dL_dS0.contiguous(), drho, du)
+        rho = None if rho is None else rho.contiguous()
+        u, dL_dS0 = u.contiguous(), dL_dS0.contiguous()
+        self._sync_in()
+        B.lbmrv_equilibrium_vjp(self.h, rho, u, dL_dS0, drho, du)
+        self._sync_out()
+        self._keep = (rho, u, dL_dS0)
         return drho, du
 
 

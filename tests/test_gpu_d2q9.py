@@ -307,3 +307,45 @@ def test_conserved_sums_with_reference_velocity():
     np.testing.assert_allclose(c0[1], (rho * ux).sum(), rtol=1e-5)
     np.testing.assert_allclose(c0[2], (rho * uy).sum(), rtol=1e-5)
     sim.close()
+
+
+def test_two_handles_on_two_streams_match_single_stream_runs():
+    """Handles are independent: a D2Q9 lattice (FP32, prescribed u~) and a D3Q19 lattice
+    (FP16, u~ = q/rho) stepped interleaved on two non-default streams end bit for bit where
+    each ends alone on the default stream."""
+    import torch
+
+    from paper_1312_3297_gb300 import D3Q19, D2Q9
+
+    rho, ux, uy = f32_fields(inp.random_sine_flow(96, 40, seed=21))
+    d3 = inp.random_flow_3d(48, 12, 10, seed=22)
+    r3, u3 = inp.to_f32_exact(d3["rho"]), inp.to_f32_exact(d3["u"])
+    s3 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
+
+    def make(stream=None):
+        a = D2Q9(96, 40, S_PAPER, mode="prescribed", stream=stream)
+        a.set_utilde(None, 0.03, 100.0)
+        a.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+        return a
+
+    def make3(stream=None):
+        b = D3Q19(48, 12, 10, s3, mode="fluid", storage="fp16", stream=stream)
+        b.init_equilibrium(torch.as_tensor(r3), *(torch.as_tensor(c) for c in u3))
+        return b
+
+    ref_a, ref_b = make(), make3()
+    ref_a.step(60)
+    ref_b.step(60)
+    want_a, want_b = ref_a.state(), ref_b.state()
+    ref_a.close()
+    ref_b.close()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    a, b = make(s1), make3(s2)
+    for _ in range(6):
+        a.step(10)
+        b.step(10)
+    got_a, got_b = a.state(), b.state()
+    torch.testing.assert_close(got_a, want_a, rtol=0, atol=0)
+    torch.testing.assert_close(got_b, want_b, rtol=0, atol=0)
+    a.close()
+    b.close()
