@@ -51,6 +51,25 @@ _lib = None
 _openmp = False
 
 
+def _compile(out_path: str, extra=()) -> bool:
+    """gcc the C oracle into out_path (OpenMP when available); returns whether OpenMP is
+    on. `extra` are additional compiler flags (the mutation tests pass a -D)."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler found to build the oracle")
+    base = [cc, "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
+            "-fno-fast-math", *extra, *_SRCS, "-o", out_path + ".tmp", "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True, text=True)
+        omp = True
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True, text=True)
+        omp = False
+    os.replace(out_path + ".tmp", out_path)
+    return omp
+
+
 def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (OpenMP when available). Returns the .so path."""
     global _openmp
@@ -59,19 +78,7 @@ def build(force: bool = False) -> str:
             and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(p) for p in _SRCS)):
         _openmp = _probe_openmp_flag()
         return _LIB_PATH
-    cc = shutil.which("gcc") or shutil.which("cc")
-    if cc is None:
-        raise RuntimeError("no C compiler found to build the oracle")
-    base = [cc, "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
-            "-fno-fast-math", *_SRCS, "-o", _LIB_PATH + ".tmp", "-lm"]
-    try:
-        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
-                       capture_output=True, text=True)
-        _openmp = True
-    except subprocess.CalledProcessError:
-        subprocess.run(base, check=True, capture_output=True, text=True)
-        _openmp = False
-    os.replace(_LIB_PATH + ".tmp", _LIB_PATH)
+    _openmp = _compile(_LIB_PATH)
     with open(_LIB_PATH + ".omp", "w") as fh:
         fh.write("1" if _openmp else "0")
     return _LIB_PATH
@@ -94,42 +101,46 @@ def lib() -> ctypes.CDLL:
     global _lib
     with _lock:
         if _lib is None:
-            path = build()
-            L = ctypes.CDLL(path)
-            D = ctypes.c_double
-            P = ctypes.POINTER(ctypes.c_double)
-            I64 = ctypes.c_int64
-            I = ctypes.c_int
-            L.orc_poly.restype = D
-            L.orc_poly.argtypes = [I, D, D, D]
-            L.orc_moment_matrix.argtypes = [D, D, D, P]
-            L.orc_shift_matrix.argtypes = [D, D, D, P]
-            L.orc_feq.argtypes = [D, D, D, D, P]
-            L.orc_lu_solve.restype = I
-            L.orc_lu_solve.argtypes = [P, P, P]
-            L.orc_collide_definition.restype = I
-            L.orc_collide_definition.argtypes = [P, D, D, D, P, P]
-            L.orc_collide_shifted.argtypes = [P, D, D, D, P, P]
-            L.orc_collide_mrt.argtypes = [P, D, P, P]
-            L.orc_collide_lattice.restype = I
-            L.orc_collide_lattice.argtypes = [I, I64, I64, D, P, I, P, D, D, I64, P, P, I]
-            L.orc_stream.argtypes = [I64, I64, P, P, I]
-            L.orc_run.restype = I
-            L.orc_run.argtypes = [I, I64, I64, D, P, I, P, D, D, I64, I64, P, P, I]
-            L.orc_init_equilibrium.argtypes = [I64, I64, D, P, P, P, P]
-            L.orc_moments.argtypes = [I64, I64, D, P, P, P, P]
-            L.orc_velocities.argtypes = [D, P, P]
-            L.orc_poly_geier.restype = D
-            L.orc_poly_geier.argtypes = [I, D, D, D]
-            L.orc_moment_matrix_geier.argtypes = [D, D, D, P]
-            L.orc_feq_product.argtypes = [D, D, D, D, P]
-            L.orc_collide_geier.restype = I
-            L.orc_collide_geier.argtypes = [P, D, D, D, P, P]
-            L.orc_collide_cascaded.restype = I
-            L.orc_collide_cascaded.argtypes = [P, D, P, P]
-            L.orc_init_equilibrium_product.argtypes = [I64, I64, D, P, P, P, P]
-            _lib = L
+            _lib = _bind(build())
     return _lib
+
+
+def _bind(path: str) -> ctypes.CDLL:
+    """Load an oracle library and declare its entry points."""
+    L = ctypes.CDLL(path)
+    D = ctypes.c_double
+    P = ctypes.POINTER(ctypes.c_double)
+    I64 = ctypes.c_int64
+    I = ctypes.c_int
+    L.orc_poly.restype = D
+    L.orc_poly.argtypes = [I, D, D, D]
+    L.orc_moment_matrix.argtypes = [D, D, D, P]
+    L.orc_shift_matrix.argtypes = [D, D, D, P]
+    L.orc_feq.argtypes = [D, D, D, D, P]
+    L.orc_lu_solve.restype = I
+    L.orc_lu_solve.argtypes = [P, P, P]
+    L.orc_collide_definition.restype = I
+    L.orc_collide_definition.argtypes = [P, D, D, D, P, P]
+    L.orc_collide_shifted.argtypes = [P, D, D, D, P, P]
+    L.orc_collide_mrt.argtypes = [P, D, P, P]
+    L.orc_collide_lattice.restype = I
+    L.orc_collide_lattice.argtypes = [I, I64, I64, D, P, I, P, D, D, I64, P, P, I]
+    L.orc_stream.argtypes = [I64, I64, P, P, I]
+    L.orc_run.restype = I
+    L.orc_run.argtypes = [I, I64, I64, D, P, I, P, D, D, I64, I64, P, P, I]
+    L.orc_init_equilibrium.argtypes = [I64, I64, D, P, P, P, P]
+    L.orc_moments.argtypes = [I64, I64, D, P, P, P, P]
+    L.orc_velocities.argtypes = [D, P, P]
+    L.orc_poly_geier.restype = D
+    L.orc_poly_geier.argtypes = [I, D, D, D]
+    L.orc_moment_matrix_geier.argtypes = [D, D, D, P]
+    L.orc_feq_product.argtypes = [D, D, D, D, P]
+    L.orc_collide_geier.restype = I
+    L.orc_collide_geier.argtypes = [P, D, D, D, P, P]
+    L.orc_collide_cascaded.restype = I
+    L.orc_collide_cascaded.argtypes = [P, D, P, P]
+    L.orc_init_equilibrium_product.argtypes = [I64, I64, D, P, P, P, P]
+    return L
 
 
 def _ptr(a: np.ndarray):

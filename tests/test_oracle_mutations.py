@@ -1,0 +1,60 @@
+"""The oracle's pins catch the mistakes they are meant to catch.
+
+Each case builds a copy of the C oracle with one planted mistake (ORACLE_MUTATION, a
+compile-time switch that is off in the oracle every other test and tool uses), points the
+oracle module at the copy, runs the pin aimed at that kind of mistake and requires it to
+fail. A control case builds the copy the same way without a mistake and requires the same
+pins to pass. Everything runs on the CPU.
+"""
+import importlib
+
+import pytest
+
+import oracle
+
+# (mutation, what is planted, pin module, pin function, pin arguments)
+CASES = [
+    (1, "the (v.u)^2 term of the equilibrium dropped", "test_oracle_pins",
+     "test_equilibrium_textbook_moments", {}),
+    (2, "transport pulling from x + v_j", "test_oracle_pins",
+     "test_transport_moves_each_population_along_its_velocity", {}),
+    (3, "transposed moment matrix in the definition stepper", "test_oracle_pins",
+     "test_collision_conserves_rho_and_q", {"method": 0}),
+    (4, "wrong sign in block C3 of Appendix A", "test_oracle_pins",
+     "test_shifted_form_equals_definition", {}),
+    (5, "rates applied to the wrong moments", "test_oracle_pins",
+     "test_zero_relative_velocity_is_mrt", {}),
+    (6, "s+ and s- swapped in Appendix B's 2x2 block", "test_oracle_geier_pins",
+     "test_cascaded_scheme_is_the_relative_velocity_scheme", {}),
+]
+
+
+@pytest.fixture()
+def oracle_variant(tmp_path):
+    """Build the oracle with -DORACLE_MUTATION=k and use it for the duration of a test."""
+    saved = oracle.lib()
+
+    def use(k):
+        path = str(tmp_path / f"liboracle_m{k}.so")
+        oracle._compile(path, [f"-DORACLE_MUTATION={k}"])
+        oracle._lib = oracle._bind(path)
+
+    yield use
+    oracle._lib = saved
+
+
+def _pin(module, name):
+    return getattr(importlib.import_module(module), name)
+
+
+@pytest.mark.parametrize("k,what,module,name,kw", CASES, ids=[c[0] for c in CASES])
+def test_pin_catches_planted_mistake(oracle_variant, k, what, module, name, kw):
+    oracle_variant(k)
+    with pytest.raises(AssertionError):
+        _pin(module, name)(oracle, **kw)
+
+
+def test_pins_pass_on_the_unmutated_copy(oracle_variant):
+    oracle_variant(0)
+    for _, _, module, name, kw in CASES:
+        _pin(module, name)(oracle, **kw)
