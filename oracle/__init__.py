@@ -140,6 +140,21 @@ def _bind(path: str) -> ctypes.CDLL:
     L.orc_collide_cascaded.restype = I
     L.orc_collide_cascaded.argtypes = [P, D, P, P]
     L.orc_init_equilibrium_product.argtypes = [I64, I64, D, P, P, P, P]
+    IP = ctypes.POINTER(ctypes.c_int)  # D3Q19 oracle (lbmrv_oracle3d.c, wrapped by d3q19.py)
+    L.orc3_velocities.argtypes = [IP, IP, IP]
+    L.orc3_poly.restype = D
+    L.orc3_poly.argtypes = [I, D, D, D, D]
+    L.orc3_moment_matrix.argtypes = [D, D, D, D, P]
+    L.orc3_feq.argtypes = [D, D, D, D, D, P]
+    L.orc3_collide_node.restype = I
+    L.orc3_collide_node.argtypes = [P, P, D, P, P]
+    L.orc3_collide_lattice.restype = I
+    L.orc3_collide_lattice.argtypes = [I64, I64, I64, D, P, I, P, D, D, I64, P, P, I]
+    L.orc3_stream.argtypes = [I64, I64, I64, P, P, I]
+    L.orc3_run.restype = I
+    L.orc3_run.argtypes = [I64, I64, I64, D, P, I, P, D, D, I64, I64, P, P, I]
+    L.orc3_init_equilibrium.argtypes = [I64, D, P, P, P]
+    L.orc3_moments.argtypes = [I64, D, P, P, P]
     return L
 
 

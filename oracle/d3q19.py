@@ -9,35 +9,9 @@ import ctypes
 
 import numpy as np
 
-from . import _f64, _optr, _ptr, lib as _lib
+from . import _f64, _optr, _ptr, lib
 
 Q = 19
-_ready = False
-
-
-def lib():
-    global _ready
-    L = _lib()
-    if not _ready:
-        D, I, I64 = ctypes.c_double, ctypes.c_int, ctypes.c_int64
-        P = ctypes.POINTER(ctypes.c_double)
-        IP = ctypes.POINTER(ctypes.c_int)
-        L.orc3_velocities.argtypes = [IP, IP, IP]
-        L.orc3_poly.restype = D
-        L.orc3_poly.argtypes = [I, D, D, D, D]
-        L.orc3_moment_matrix.argtypes = [D, D, D, D, P]
-        L.orc3_feq.argtypes = [D, D, D, D, D, P]
-        L.orc3_collide_node.restype = I
-        L.orc3_collide_node.argtypes = [P, P, D, P, P]
-        L.orc3_collide_lattice.restype = I
-        L.orc3_collide_lattice.argtypes = [I64, I64, I64, D, P, I, P, D, D, I64, P, P, I]
-        L.orc3_stream.argtypes = [I64, I64, I64, P, P, I]
-        L.orc3_run.restype = I
-        L.orc3_run.argtypes = [I64, I64, I64, D, P, I, P, D, D, I64, I64, P, P, I]
-        L.orc3_init_equilibrium.argtypes = [I64, D, P, P, P]
-        L.orc3_moments.argtypes = [I64, D, P, P, P]
-        _ready = True
-    return L
 
 
 def velocities():
