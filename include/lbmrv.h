@@ -24,7 +24,10 @@
  *     lbmrv_create and lbmrv_set_utilde, which must outlive the handle (or the next
  *     lbmrv_set_utilde call).
  *   - Work is enqueued on the handle's CUDA stream and returns without synchronising,
- *     except the calls documented as synchronous (they return host values).
+ *     except the calls documented as synchronous (they return host values). Step kernels
+ *     are launched with programmatic dependent launch: one may be scheduled while the work
+ *     before it in the stream finishes, but it touches no memory until that work has
+ *     completed, so stream order means what it always does.
  *   - Lattice layout: periodic D2Q9 (dims = {nx, ny, 1}) or D3Q19 (dims = {nx, ny, nz}),
  *     lattice units dx = 1 (so dt = 1/lambda, relation (lambda)). Node (x, y, z) has index
  *     i = (z*ny + y)*nx + x; n = nx*ny*nz. Population state: structure of arrays, q planes
