@@ -227,6 +227,182 @@ __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict_
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// 16-bit D3Q19 step with the next row staged in shared memory. Each warp owns a sequence of
+// row segments of 256 nodes (32 lanes x 8-node packs); while it relaxes one, asynchronous
+// copies (cp.async) bring the next one's 19 plane segments, plus for every x-moving plane
+// the 4-byte word that holds the element across the pack boundary, into the other half of
+// its double buffer. Memory parallelism then no longer depends on registers, and the
+// kernel runs two 4-warp blocks per SM with up to 255 registers per thread.
+constexpr int kPipeWarps = 4;
+constexpr int kPipeSeg = 32 * 8;                               // nodes per row segment
+constexpr int kPipeData = 19 * 32 * 16;                        // packs of one stage
+constexpr int kPipeStage = kPipeData + 10 * 32 * 4;            // + halo words
+constexpr int kPipeSmem = kPipeWarps * 2 * kPipeStage;         // bytes per block
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_prev() {  // all but the latest group complete
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+}
+
+// Source row of plane j among the nine rows of the (y, z) neighbourhood, and its x shift:
+// 0 none, 1 from the left (x - 1), 2 from the right (x + 1); relation (transport) in pull
+// form. hslot: the plane's halo slot (x-moving planes only).
+__device__ __forceinline__ int64_t plane_row(const Rows3& r, int j) {
+    switch (j) {
+        case 0: case 1: case 2: return r.r00;
+        case 3: case 7: case 10: return r.rm0;
+        case 4: case 8: case 9: return r.rp0;
+        case 5: case 11: case 14: return r.r0m;
+        case 6: case 12: case 13: return r.r0p;
+        case 15: return r.rmm;
+        case 16: return r.rpp;
+        case 17: return r.rmp;
+        default: return r.rpm;
+    }
+}
+__host__ __device__ constexpr int plane_shift(int j) {
+    return (j == 1 || j == 7 || j == 9 || j == 11 || j == 13) ? 1
+         : (j == 2 || j == 8 || j == 10 || j == 12 || j == 14) ? 2 : 0;
+}
+__host__ __device__ constexpr int plane_hslot(int j) {
+    return j == 1 ? 0 : j == 7 ? 1 : j == 9 ? 2 : j == 11 ? 3 : j == 13 ? 4
+         : j == 2 ? 5 : j == 8 ? 6 : j == 10 ? 7 : j == 12 ? 8 : j == 14 ? 9 : -1;
+}
+
+template <typename T, int UM, int RCP>
+__global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __restrict__ src,
+                                                                   T* __restrict__ dst,
+                                                                   StepArgs3 a) {
+    pdl_wait_prior();
+    pdl_allow_next();
+    extern __shared__ __align__(16) unsigned char pipe_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int segs = (nx + kPipeSeg - 1) / kPipeSeg;
+    const int64_t items = (int64_t)ny * nz * segs;
+    const int64_t nwarps = (int64_t)gridDim.x * kPipeWarps;
+    unsigned char* wbuf = pipe_smem + warp * 2 * kPipeStage;
+
+    // work item -> row (y, z) and this lane's pack start x0
+    auto decode = [&](int64_t it, int& y, int& z, int& x0) {
+        const int64_t row = it / segs;
+        const int seg = (int)(it - row * segs);
+        z = (int)(row / ny);
+        y = (int)(row - (int64_t)z * ny);
+        x0 = seg * kPipeSeg + lane * 8;
+    };
+    // queue the copies of work item `it` into buffer `stage`, as one commit group
+    auto issue = [&](int64_t it, int stage) {
+        int y, z, x0;
+        decode(it, y, z, x0);
+        if (x0 < nx) {
+            const Rows3 r(y, z, nx, ny, nz);
+            unsigned char* sb = wbuf + stage * kPipeStage;
+            const int xl = (x0 == 0 ? nx : x0) - 2;   // word (x0-2, x0-1), periodic
+            const int xr = x0 + 8 >= nx ? 0 : x0 + 8;  // word (x0+8, x0+9), periodic
+#pragma unroll
+            for (int j = 0; j < 19; ++j) {
+                const T* row = src + j * n + plane_row(r, j);
+                cp_async16(sb + (j * 32 + lane) * 16, row + x0);
+                if (plane_hslot(j) >= 0)
+                    cp_async4(sb + kPipeData + (plane_hslot(j) * 32 + lane) * 4,
+                              row + (plane_shift(j) == 1 ? xl : xr));
+            }
+        }
+        cp_async_commit();
+    };
+
+    int64_t it = (int64_t)blockIdx.x * kPipeWarps + warp;
+    int stage = 0;
+    if (it < items) issue(it, 0);
+    while (it < items) {
+        const int64_t next = it + nwarps;
+        if (next < items)
+            issue(next, stage ^ 1);
+        else
+            cp_async_commit();  // an empty group keeps the wait below uniform
+        cp_async_wait_prev();
+        __syncwarp();
+        int y, z, x0;
+        decode(it, y, z, x0);
+        if (x0 < nx) {
+            const unsigned char* sb = wbuf + stage * kPipeStage;
+            const int64_t r00 = ((int64_t)z * ny + y) * nx;
+            uint32_t w[19][4];
+#pragma unroll
+            for (int j = 0; j < 19; ++j) {
+                const uint4 v = *reinterpret_cast<const uint4*>(sb + (j * 32 + lane) * 16);
+                const uint32_t hw = plane_hslot(j) >= 0
+                    ? *reinterpret_cast<const uint32_t*>(sb + kPipeData +
+                                                         (plane_hslot(j) * 32 + lane) * 4)
+                    : 0u;
+                if (plane_shift(j) == 1) {         // elements (x0-1, ..., x0+6)
+                    w[j][0] = __byte_perm(hw >> 16, v.x, 0x5410);
+                    w[j][1] = __byte_perm(v.x, v.y, 0x5432);
+                    w[j][2] = __byte_perm(v.y, v.z, 0x5432);
+                    w[j][3] = __byte_perm(v.z, v.w, 0x5432);
+                } else if (plane_shift(j) == 2) {  // elements (x0+1, ..., x0+8)
+                    w[j][0] = __byte_perm(v.x, v.y, 0x5432);
+                    w[j][1] = __byte_perm(v.y, v.z, 0x5432);
+                    w[j][2] = __byte_perm(v.z, v.w, 0x5432);
+                    w[j][3] = __byte_perm(v.w, hw, 0x5432);
+                } else {
+                    w[j][0] = v.x;
+                    w[j][1] = v.y;
+                    w[j][2] = v.z;
+                    w[j][3] = v.w;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t i = r00 + x0 + 2 * k;  // first node of the pair
+                F2 h[19];
+#pragma unroll
+                for (int j = 0; j < 19; ++j) {
+                    const float2 f = Cvt16<T>::unpack(w[j][k]);
+                    h[j] = pack2(f.x, f.y);
+                }
+                F2 ux(0.0f), uy(0.0f), uz(0.0f);
+                if constexpr (UM != UM_ZERO && UM != UM_FLUID) {
+                    const F2 amp(a.amp_t);
+                    ux = amp * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
+                    uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
+                    uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
+                }
+                // the same arithmetic as k_step3_r16 (increments added to the re-read pair),
+                // so that both kernels give the same bits
+                relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                for (int j = 0; j < 19; ++j) {
+                    uint32_t wj;
+                    asm volatile("mov.b32 %0, %1;" : "=r"(wj) : "r"(w[j][k]));
+                    const float2 f = Cvt16<T>::unpack(wj);
+                    float lo, hi;
+                    unpack2(pack2(f.x, f.y) + h[j], lo, hi);
+                    w[j][k] = Cvt16<T>::pack(lo, hi);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 19; ++j) store_raw16<8>(dst + j * n + r00 + x0, w[j]);
+        }
+        __syncwarp();  // every lane is done with `stage` before it is refilled
+        it = next;
+        stage ^= 1;
+    }
+}
+
 __constant__ int kC3X[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ int kC3Y[19] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ int kC3Z[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
@@ -382,9 +558,31 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 constexpr int kPairs3 = 2;
 constexpr int kRcp3 = RCP_RN;
 
+// Whether 8-node 16-bit packs run the shared-memory pipeline (k_step3_pipe).
+constexpr bool kPipe3 = true;
+
+template <typename T, int UM>
+cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st) {
+    auto kernel = k_step3_pipe<T, UM, kRcp3>;
+    cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
+    int dev = 0, sms = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int64_t segs = (a.nx + kPipeSeg - 1) / kPipeSeg;
+    const int64_t items = (int64_t)a.ny * a.nz * segs;
+    const int64_t need = (items + kPipeWarps - 1) / kPipeWarps;
+    const int blocks = (int)(need < 2LL * sms ? need : 2LL * sms);  // persistent: 2 per SM
+    e = launch_pdl_smem(kernel, dim3(blocks), dim3(kPipeWarps * 32), kPipeSmem, st,
+                        static_cast<const T*>(src), static_cast<T*>(dst), a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <typename T, int UM>
 cudaError_t step3_nv(const void* src, void* dst, const StepArgs3& a, cudaStream_t st, int nv) {
     if constexpr (sizeof(T) == 2) {
+        if (nv == 8 && kPipe3) return launch_pipe3<T, UM>(src, dst, a, st);
         if (nv == 4)
             return launch3(k_step3_r16<T, 4, UM, kPairs3, kRcp3>, src, dst, a, st, nv, true);
         if (nv == 8)
