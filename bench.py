@@ -134,12 +134,19 @@ class ClockSampler:
         smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        power = []
+        for r in rows:
+            try:
+                power.append(float(r[3].split()[0]))
+            except (ValueError, IndexError):
+                pass
         try:
             os.unlink(self.path)
         except OSError:
             pass
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "power_w": round(statistics.median(power), 1) if power else None,
                 "samples": len(rows)}
 
 
@@ -172,10 +179,22 @@ def job_mlups(nodes_per_rank: int, world: int, steps: int, ms_max: float) -> flo
 
 def default_width(lattice: str, storage: str, nx: int) -> int:
     """Nodes per thread of the automatically chosen step kernel (the library's rule)."""
-    widest = (4 if storage == "fp32" else 8) if lattice == "d2q9" else (4 if storage == "fp32" else 2)
+    widest = 4 if storage == "fp32" else 8
     while widest > 1 and nx % widest:
         widest //= 2
     return widest
+
+
+def kernel_label(lattice: str, storage: str, nx: int, mode: str) -> str:
+    """Name of the step kernel the library launches for this configuration."""
+    nv = default_width(lattice, storage, nx)
+    if lattice == "d2q9":
+        name = "k_step_vec"
+    elif storage == "fp32":
+        name = "k_step3"
+    else:
+        name = {8: "k_step3_pipe", 4: "k_step3_r16"}.get(nv, "k_step3")
+    return f"{name}<{storage},{nv},{mode}>"
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -314,9 +333,7 @@ def gpu_arm(args):
                          "traffic": recorded_traffic() if headline else None,
                          "peak_kind": peak_kind,
                          "frac_of_nominal_7900": round(achieved / 7900.0, 4),
-                         "kernel": (f"{'k_step_vec' if args.lattice == 'd2q9' else 'k_step3'}"
-                                    f"<{args.storage},{default_width(args.lattice, args.storage, size)},"
-                                    f"{args.mode}>")},
+                         "kernel": kernel_label(args.lattice, args.storage, size, args.mode)},
             "clocks": clock_info,
             "e2e": e2e,
             "gpu_launches": args.steps,

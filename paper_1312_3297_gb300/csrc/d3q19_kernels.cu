@@ -233,12 +233,16 @@ __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict_
 // copies (cp.async) bring the next one's 19 plane segments, plus for every x-moving plane
 // the 4-byte word that holds the element across the pack boundary, into the other half of
 // its double buffer. Memory parallelism then no longer depends on registers, and the
-// kernel runs two 4-warp blocks per SM with up to 255 registers per thread.
-constexpr int kPipeWarps = 4;
+// kernel runs two 4-warp blocks per SM with up to 255 registers per thread (measured on
+// GB300: more warps with fewer registers spill, and deeper rings with fewer warps issue
+// too slowly).
 constexpr int kPipeSeg = 32 * 8;                               // nodes per row segment
 constexpr int kPipeData = 19 * 32 * 16;                        // packs of one stage
 constexpr int kPipeStage = kPipeData + 10 * 32 * 4;            // + halo words
-constexpr int kPipeSmem = kPipeWarps * 2 * kPipeStage;         // bytes per block
+
+constexpr int kPipeWarps = 4;                                   // per block, 2 blocks per SM
+constexpr int kPipeStages = 2;                                  // segments per warp
+constexpr int kPipeSmem = kPipeWarps * kPipeStages * kPipeStage;  // bytes per block
 
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
@@ -251,14 +255,37 @@ __device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
-__device__ __forceinline__ void cp_async_wait_prev() {  // all but the latest group complete
-    asm volatile("cp.async.wait_group 1;" ::: "memory");
+template <int N>
+__device__ __forceinline__ void cp_async_wait_all_but() {  // all but the latest N groups
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Source row of plane j among the nine rows of the (y, z) neighbourhood, and its x shift:
-// 0 none, 1 from the left (x - 1), 2 from the right (x + 1); relation (transport) in pull
-// form. hslot: the plane's halo slot (x-moving planes only).
-__device__ __forceinline__ int64_t plane_row(const Rows3& r, int j) {
+// x shift of plane j: 0 none, 1 from the left (x - 1), 2 from the right (x + 1); relation
+// (transport) in pull form. hslot: the plane's halo slot (x-moving planes only).
+__host__ __device__ constexpr int plane_shift(int j) {
+    return (j == 1 || j == 7 || j == 9 || j == 11 || j == 13) ? 1
+         : (j == 2 || j == 8 || j == 10 || j == 12 || j == 14) ? 2 : 0;
+}
+__host__ __device__ constexpr int plane_hslot(int j) {
+    return j == 1 ? 0 : j == 7 ? 1 : j == 9 ? 2 : j == 11 ? 3 : j == 13 ? 4
+         : j == 2 ? 5 : j == 8 ? 6 : j == 10 ? 7 : j == 12 ? 8 : j == 14 ? 9 : -1;
+}
+
+// Rows of the (y, z) neighbourhood as row numbers z * ny + y (the launcher checks that
+// ny * nz fits in 31 bits), periodic.
+struct RowNums3 {
+    int r00, rm0, rp0, r0m, r0p, rmm, rpp, rmp, rpm;
+    __device__ __forceinline__ RowNums3(int y, int z, int ny, int nz) {
+        const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+        const int zr = z * ny, zmr = (z == 0 ? nz - 1 : z - 1) * ny;
+        const int zpr = (z == nz - 1 ? 0 : z + 1) * ny;
+        r00 = zr + y, rm0 = zr + ym, rp0 = zr + yp;
+        r0m = zmr + y, r0p = zpr + y;
+        rmm = zmr + ym, rpp = zpr + yp, rmp = zpr + ym, rpm = zmr + yp;
+    }
+};
+// Source row of plane j among the nine rows of the (y, z) neighbourhood.
+__device__ __forceinline__ int plane_rownum(const RowNums3& r, int j) {
     switch (j) {
         case 0: case 1: case 2: return r.r00;
         case 3: case 7: case 10: return r.rm0;
@@ -271,19 +298,12 @@ __device__ __forceinline__ int64_t plane_row(const Rows3& r, int j) {
         default: return r.rpm;
     }
 }
-__host__ __device__ constexpr int plane_shift(int j) {
-    return (j == 1 || j == 7 || j == 9 || j == 11 || j == 13) ? 1
-         : (j == 2 || j == 8 || j == 10 || j == 12 || j == 14) ? 2 : 0;
-}
-__host__ __device__ constexpr int plane_hslot(int j) {
-    return j == 1 ? 0 : j == 7 ? 1 : j == 9 ? 2 : j == 11 ? 3 : j == 13 ? 4
-         : j == 2 ? 5 : j == 8 ? 6 : j == 10 ? 7 : j == 12 ? 8 : j == 14 ? 9 : -1;
-}
 
 template <typename T, int UM, int RCP>
 __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __restrict__ src,
                                                                    T* __restrict__ dst,
                                                                    StepArgs3 a) {
+    constexpr int S = kPipeStages;
     pdl_wait_prior();
     pdl_allow_next();
     extern __shared__ __align__(16) unsigned char pipe_smem[];
@@ -291,30 +311,45 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n = (int64_t)nx * ny * nz;
     const int segs = (nx + kPipeSeg - 1) / kPipeSeg;
-    const int64_t items = (int64_t)ny * nz * segs;
-    const int64_t nwarps = (int64_t)gridDim.x * kPipeWarps;
-    unsigned char* wbuf = pipe_smem + warp * 2 * kPipeStage;
+    unsigned char* wbuf = pipe_smem + warp * S * kPipeStage;
 
-    // work item -> row (y, z) and this lane's pack start x0
-    auto decode = [&](int64_t it, int& y, int& z, int& x0) {
-        const int64_t row = it / segs;
-        const int seg = (int)(it - row * segs);
-        z = (int)(row / ny);
-        y = (int)(row - (int64_t)z * ny);
-        x0 = seg * kPipeSeg + lane * 8;
+    // Warp w takes work items (row segments, x fastest, then y, z) w, w + W, w + 2W, ...
+    // (W warps in the grid), so that the warps in flight read neighbouring rows. A cursor
+    // (seg, y, z) steps by W in mixed radix (segs, ny, nz), so no item index is divided.
+    const int64_t nwarps = (int64_t)gridDim.x * kPipeWarps;
+    struct Cursor {
+        int seg, y, z;
     };
-    // queue the copies of work item `it` into buffer `stage`, as one commit group
-    auto issue = [&](int64_t it, int stage) {
-        int y, z, x0;
-        decode(it, y, z, x0);
+    auto split = [&](int64_t it) {
+        const int64_t row = it / segs;
+        Cursor c;
+        c.seg = (int)(it - row * segs);
+        c.z = (int)(row / ny);
+        c.y = (int)(row - (int64_t)c.z * ny);
+        return c;
+    };
+    const Cursor step = split(nwarps);
+    auto advance = [&](Cursor c) {
+        c.seg += step.seg;
+        int carry = c.seg >= segs;
+        c.seg -= carry ? segs : 0;
+        c.y += step.y + carry;
+        carry = c.y >= ny;
+        c.y -= carry ? ny : 0;
+        c.z += step.z + carry;
+        return c;
+    };
+    // queue the copies of the item at `c` into buffer `stage`, as one commit group
+    auto issue = [&](const Cursor& c, int stage) {
+        const int x0 = c.seg * kPipeSeg + lane * 8;
         if (x0 < nx) {
-            const Rows3 r(y, z, nx, ny, nz);
+            const RowNums3 r(c.y, c.z, ny, nz);
             unsigned char* sb = wbuf + stage * kPipeStage;
             const int xl = (x0 == 0 ? nx : x0) - 2;   // word (x0-2, x0-1), periodic
             const int xr = x0 + 8 >= nx ? 0 : x0 + 8;  // word (x0+8, x0+9), periodic
 #pragma unroll
             for (int j = 0; j < 19; ++j) {
-                const T* row = src + j * n + plane_row(r, j);
+                const T* row = src + j * n + (int64_t)plane_rownum(r, j) * nx;
                 cp_async16(sb + (j * 32 + lane) * 16, row + x0);
                 if (plane_hslot(j) >= 0)
                     cp_async4(sb + kPipeData + (plane_hslot(j) * 32 + lane) * 4,
@@ -324,22 +359,32 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
         cp_async_commit();
     };
 
-    int64_t it = (int64_t)blockIdx.x * kPipeWarps + warp;
-    int stage = 0;
-    if (it < items) issue(it, 0);
-    while (it < items) {
-        const int64_t next = it + nwarps;
-        if (next < items)
-            issue(next, stage ^ 1);
+    // S-stage ring: the copies of the next S - 1 items are in flight while one is relaxed
+    Cursor cur = split((int64_t)blockIdx.x * kPipeWarps + warp), ahead = cur;
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        if (ahead.z < nz)
+            issue(ahead, s);
         else
-            cp_async_commit();  // an empty group keeps the wait below uniform
-        cp_async_wait_prev();
+            cp_async_commit();  // empty groups keep the count of groups uniform
+        ahead = advance(ahead);
+    }
+    int stage = 0, fill = S - 1;
+    while (cur.z < nz) {
+        if (ahead.z < nz)
+            issue(ahead, fill);
+        else
+            cp_async_commit();
+        ahead = advance(ahead);
+        fill = fill == S - 1 ? 0 : fill + 1;
+        cp_async_wait_all_but<S - 1>();  // the oldest group: the item at `cur`
         __syncwarp();
-        int y, z, x0;
-        decode(it, y, z, x0);
+        const int y = cur.y, z = cur.z, x0 = cur.seg * kPipeSeg + lane * 8;
         if (x0 < nx) {
             const unsigned char* sb = wbuf + stage * kPipeStage;
-            const int64_t r00 = ((int64_t)z * ny + y) * nx;
+            const int64_t r00 = (int64_t)(z * ny + y) * nx;
+            // pair k of an x-moving plane straddles words k and k + 1 of (left halo, pack)
+            // or (pack, right halo)
             uint32_t w[19][4];
 #pragma unroll
             for (int j = 0; j < 19; ++j) {
@@ -348,22 +393,12 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
                     ? *reinterpret_cast<const uint32_t*>(sb + kPipeData +
                                                          (plane_hslot(j) * 32 + lane) * 4)
                     : 0u;
-                if (plane_shift(j) == 1) {         // elements (x0-1, ..., x0+6)
-                    w[j][0] = __byte_perm(hw >> 16, v.x, 0x5410);
-                    w[j][1] = __byte_perm(v.x, v.y, 0x5432);
-                    w[j][2] = __byte_perm(v.y, v.z, 0x5432);
-                    w[j][3] = __byte_perm(v.z, v.w, 0x5432);
-                } else if (plane_shift(j) == 2) {  // elements (x0+1, ..., x0+8)
-                    w[j][0] = __byte_perm(v.x, v.y, 0x5432);
-                    w[j][1] = __byte_perm(v.y, v.z, 0x5432);
-                    w[j][2] = __byte_perm(v.z, v.w, 0x5432);
-                    w[j][3] = __byte_perm(v.w, hw, 0x5432);
-                } else {
-                    w[j][0] = v.x;
-                    w[j][1] = v.y;
-                    w[j][2] = v.z;
-                    w[j][3] = v.w;
-                }
+                const uint32_t e[6] = {hw, v.x, v.y, v.z, v.w, hw};
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    w[j][k] = plane_shift(j) == 1 ? __byte_perm(e[k], e[k + 1], 0x5432)
+                            : plane_shift(j) == 2 ? __byte_perm(e[k + 1], e[k + 2], 0x5432)
+                                                  : e[k + 1];
             }
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -398,8 +433,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
             for (int j = 0; j < 19; ++j) store_raw16<8>(dst + j * n + r00 + x0, w[j]);
         }
         __syncwarp();  // every lane is done with `stage` before it is refilled
-        it = next;
-        stage ^= 1;
+        cur = advance(cur);
+        stage = stage == S - 1 ? 0 : stage + 1;
     }
 }
 
@@ -566,14 +601,21 @@ cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStr
     auto kernel = k_step3_pipe<T, UM, kRcp3>;
     cudaError_t e =
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, per_sm = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPipeWarps * 32,
+                                                          kPipeSmem);
     if (e != cudaSuccess) return e;
+    // persistent: no more blocks than are resident at once (work is split between warps
+    // up front)
+    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
     const int64_t segs = (a.nx + kPipeSeg - 1) / kPipeSeg;
     const int64_t items = (int64_t)a.ny * a.nz * segs;
     const int64_t need = (items + kPipeWarps - 1) / kPipeWarps;
-    const int blocks = (int)(need < 2LL * sms ? need : 2LL * sms);  // persistent: 2 per SM
+    const int64_t full = (int64_t)per_sm * sms;
+    const int blocks = (int)(need < full ? need : full);
     e = launch_pdl_smem(kernel, dim3(blocks), dim3(kPipeWarps * 32), kPipeSmem, st,
                         static_cast<const T*>(src), static_cast<T*>(dst), a);
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -582,7 +624,8 @@ cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStr
 template <typename T, int UM>
 cudaError_t step3_nv(const void* src, void* dst, const StepArgs3& a, cudaStream_t st, int nv) {
     if constexpr (sizeof(T) == 2) {
-        if (nv == 8 && kPipe3) return launch_pipe3<T, UM>(src, dst, a, st);
+        if (nv == 8 && kPipe3 && (int64_t)a.ny * a.nz < (1LL << 31))
+            return launch_pipe3<T, UM>(src, dst, a, st);
         if (nv == 4)
             return launch3(k_step3_r16<T, 4, UM, kPairs3, kRcp3>, src, dst, a, st, nv, true);
         if (nv == 8)

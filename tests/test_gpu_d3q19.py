@@ -60,6 +60,17 @@ def test_16bit_3d_every_width(storage, tol, mode):
     np.testing.assert_array_equal(outs[8], outs[4])
 
 
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("shape", [(264, 3, 2), (552, 2, 3)])
+def test_16bit_3d_rows_of_several_segments(storage, tol, shape):
+    """Rows longer than one 256-node segment of the staged 8-node-pack kernel, the last
+    segment short (one pack; five packs), with every x-moving population crossing the
+    segment boundaries: the kernel against the oracle and bit for bit against 4-node packs."""
+    outs = {w: _check(shape, "fluid", 12, tol=tol, seed=5, storage=storage, width=w)
+            for w in (4, 8)}
+    np.testing.assert_array_equal(outs[8], outs[4])
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (7, 3, 2), (2, 9, 1), (5, 1, 4)])
 def test_parity_degenerate_3d(shape):
     for mode in ("zero", "fluid", "prescribed"):
