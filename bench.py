@@ -507,16 +507,20 @@ def e2e_measure(torch, D2Q9, inp, fields, steps):
     sim.step(3)
     sim.moments_host(rho_o, u_o)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sim.init_equilibrium_host(rho_h, u_h)
-    sim.step(steps)
-    sim.moments_host(rho_o, u_o)  # synchronous
-    dt = time.perf_counter() - t0
+    runs = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        sim.init_equilibrium_host(rho_h, u_h)
+        sim.step(steps)
+        sim.moments_host(rho_o, u_o)  # synchronous
+        runs.append(n * steps / (time.perf_counter() - t0) / 1e6)
     sim.close()
-    return {"value": round(n * steps / dt / 1e6, 1), "unit": "MLUPS",
+    return {"value": round(statistics.median(runs), 1), "unit": "MLUPS",
             "h2d_bytes_per_step": round(12 * n / steps, 1),
             "d2h_bytes_per_step": round(12 * n / steps, 1),
-            "unit_of_work": f"one {steps}-step run from host rho,u to host rho,u"}
+            "unit_of_work": f"one {steps}-step run from host rho,u to host rho,u "
+                            "(median of 3 runs)",
+            "runs": [round(r, 1) for r in runs]}
 
 
 # ------------------------------------------------------------------ CPU oracle

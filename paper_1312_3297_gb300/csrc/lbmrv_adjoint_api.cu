@@ -5,6 +5,7 @@
 #include "handle.h"
 #include "launch.h"
 #include "lbmrv.h"
+#include "trace.h"
 
 using namespace lbmrv;
 
@@ -72,6 +73,7 @@ int64_t lbmrv_adjoint_workspace_bytes(lbmrv_t h, int64_t n, int64_t seg) {
 
 int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
                                size_t ws_bytes) {
+    lbmrv::TraceRange trace("lbmrv_forward_checkpointed");
     WsLayout L;
     int rc = check_common(h, n, seg, ws_dev, ws_bytes, "lbmrv_forward_checkpointed", &L);
     if (rc != LBMRV_OK) return rc;
@@ -115,6 +117,7 @@ int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
 int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_bytes,
                   const float* dL_dS_dev, float* dL_dS0_dev, double* dL_ds_host,
                   double* dL_damp_host, float* dL_dut0_dev) {
+    lbmrv::TraceRange trace("lbmrv_adjoint");
     WsLayout L;
     int rc = check_common(h, n, seg, ws_dev, ws_bytes, "lbmrv_adjoint", &L);
     if (rc != LBMRV_OK) return rc;

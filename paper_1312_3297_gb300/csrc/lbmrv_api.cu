@@ -11,6 +11,7 @@
 #include "handle.h"
 #include "launch.h"
 #include "lbmrv.h"
+#include "trace.h"
 
 using namespace lbmrv;
 
@@ -289,6 +290,7 @@ int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u
 }
 
 int lbmrv_step(lbmrv_t h, int64_t n) {
+    lbmrv::TraceRange trace("lbmrv_step");
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_step: NULL handle");
     if (n < 0) return fail(h, LBMRV_E_INVAL, "lbmrv_step: n < 0");
     if (h->lattice == LBMRV_D3Q19 && h->umode == LBMRV_UT_PRESCRIBED && !h->ut0)
@@ -336,6 +338,7 @@ int lbmrv_moments_host(lbmrv_t h, float* rho_host, float* u_host) {
 }
 
 int lbmrv_conserved3(lbmrv_t h, double out_host[5]) {
+    lbmrv::TraceRange trace("lbmrv_conserved");
     if (!h || !out_host) return fail(h, LBMRV_E_INVAL, "lbmrv_conserved3: NULL argument");
     DeviceGuard g(h->device);
     double* res = h->red + 8 * (size_t)h->red_blocks;
