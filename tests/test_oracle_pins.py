@@ -402,6 +402,29 @@ def test_shear_wave_viscosity_second_order(orc):
     assert abs(nu_other / ((1 / 1.2 - 0.5) / 3) - 1) < 0.01
 
 
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_taylor_green_decay_rate(orc, mode):
+    """Section 2.3: with the MRT viscosity nu = (1/s_nu - 1/2) / 3 (lambda = dx = 1), a
+    small Taylor-Green vortex decays as exp(-2 nu k^2 t), k = 2 pi / L, for every u~."""
+    L, s_nu, u0 = 32, 1.5, 1e-4
+    s = np.array([0, 0, 0, 1.4, s_nu, s_nu, 1.2, 1.2, 1.4])
+    d = inp.taylor_green(L, L, u0=u0)
+    f = orc.init_equilibrium(d["rho"], d["ux"], d["uy"], 1.0)
+    k = 2 * np.pi / L
+    x = np.arange(L)[None, :]
+    y = np.arange(L)[:, None]
+    shape = -np.cos(k * x) * np.sin(k * y)
+    ts, amps, t = [], [], 0
+    for chunk in (40, 20, 20, 20, 20):
+        f = orc.run(f, 1.0, s, mode, chunk, t0=t, amp=0.02, period=0.0, nthreads=4)
+        t += chunk
+        _, ux, _ = orc.moments(f, 1.0)
+        ts.append(t)
+        amps.append((ux * shape).sum() / (shape * shape).sum())
+    nu = -np.polyfit(ts, np.log(amps), 1)[0] / (2 * k * k)
+    assert abs(nu / ((1 / s_nu - 0.5) / 3) - 1) < 1e-3, nu
+
+
 @pytest.mark.slow
 def test_advection_direction(orc):
     """A transverse wave on a uniform flow U moves with the flow (Euler limit of Section
