@@ -84,7 +84,7 @@ template <typename T> __device__ __forceinline__ float to_f(T v);
 template <> __device__ __forceinline__ float to_f<float>(float v) { return v; }
 template <> __device__ __forceinline__ float to_f<__half>(__half v) { return __half2float(v); }
 template <> __device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 v) {
-    return __bfloat162float(v);
+    return __uint_as_float((uint32_t)__bfloat16_as_ushort(v) << 16);  // the upper half
 }
 
 template <typename T> __device__ __forceinline__ T from_f(float v);

@@ -65,14 +65,16 @@ struct PackCvt<__nv_bfloat16, NV> {
     static_assert(NV == 1 || NV % 2 == 0, "16-bit packs convert in pairs");
     __device__ __forceinline__ static void in(const Pack<__nv_bfloat16, NV>& pk, float out[NV]) {
         if constexpr (NV == 1) {
-            out[0] = __bfloat162float(pk.v[0]);
+            out[0] = __uint_as_float((uint32_t)__bfloat16_as_ushort(pk.v[0]) << 16);
         } else {
 #pragma unroll
             for (int k = 0; k < NV; k += 2) {
-                const float2 f =
-                    __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&pk.v[k]));
-                out[k] = f.x;
-                out[k + 1] = f.y;
+                // a BF16 value is the upper half of the FP32 value: two integer operations
+                // (measured faster at 8192^2 than the conversion intrinsic, same bits)
+                uint32_t w;
+                memcpy(&w, &pk.v[k], 4);
+                out[k] = __uint_as_float(w << 16);
+                out[k + 1] = __uint_as_float(w & 0xffff0000u);
             }
         }
     }
