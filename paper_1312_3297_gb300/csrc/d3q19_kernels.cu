@@ -57,6 +57,36 @@ struct Rows3 {
     }
 };
 
+// Stored pair w plus the increments inc, rounded once to storage form. The 16-bit values
+// enter FP32 additions directly (add.f32.f16 / add.f32.bf16, sm_100 and later): the same
+// exact widening and single rounding as converting first, in one instruction per value.
+template <typename T>
+struct MixedAdd;
+template <>
+struct MixedAdd<__half> {
+    __device__ __forceinline__ static float add(unsigned short v, float c) {
+        float d;
+        asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(d) : "h"(v), "f"(c));
+        return d;
+    }
+};
+template <>
+struct MixedAdd<__nv_bfloat16> {
+    __device__ __forceinline__ static float add(unsigned short v, float c) {
+        float d;
+        asm("add.rn.f32.bf16 %0, %1, %2;" : "=f"(d) : "h"(v), "f"(c));
+        return d;
+    }
+};
+template <typename T>
+__device__ __forceinline__ uint32_t add_to_pair(uint32_t w, F2 inc) {
+    unsigned short lo, hi;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(w));
+    float a, b;
+    unpack2(inc, a, b);
+    return Cvt16<T>::pack(MixedAdd<T>::add(lo, a), MixedAdd<T>::add(hi, b));
+}
+
 // Thread blocks of 32 to kThreads3 threads (a multiple of 32) along one row, each thread
 // owning NV consecutive nodes, sized to the row so that short rows leave no warp idle; the
 // row index stays uniform across the block (its offsets are computed once per warp, in
@@ -121,7 +151,7 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
 // work) at the register cost of narrow ones. PAIRS: 0 relaxes node by node, converting
 // each value on its own; 1 converts a node pair at once and relaxes its two nodes; 2
 // relaxes the pair by packed FP32 instructions (F2), as an increment added to the pair
-// re-read from its packed word. Registers are capped at 128 per thread (four 128-thread
+// held in its packed word. Registers are capped at 128 per thread (four 128-thread
 // blocks per SM). Blocks span several rows when a row has fewer
 // than 128 packs (a warp stays within one row); with the row index per thread the
 // compiler spills less than with one row per block (measured).
@@ -191,16 +221,8 @@ __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict_
                         }
                         relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
 #pragma unroll
-                        for (int j = 0; j < 19; ++j) {
-                            // re-read the stored pair: the opaque copy keeps the compiler from
-                            // holding the unpacked inputs in registers through the relaxation
-                            uint32_t wj;
-                            asm volatile("mov.b32 %0, %1;" : "=r"(wj) : "r"(w[j][k]));
-                            const float2 f = Cvt16<T>::unpack(wj);
-                            float lo, hi;
-                            unpack2(pack2(f.x, f.y) + h[j], lo, hi);
-                            w[j][k] = Cvt16<T>::pack(lo, hi);
-                        }
+                        for (int j = 0; j < 19; ++j)  // the stored pair plus its increments
+                            w[j][k] = add_to_pair<T>(w[j][k], h[j]);
                     } else {
                         float h0[19], h1[19];
 #pragma unroll
@@ -448,18 +470,11 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
                     uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
                     uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
                 }
-                // the same arithmetic as k_step3_r16 (increments added to the re-read pair),
+                // the same arithmetic as k_step3_r16 (increments added to the stored pair),
                 // so that both kernels give the same bits
                 relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
 #pragma unroll
-                for (int j = 0; j < 19; ++j) {
-                    uint32_t wj;
-                    asm volatile("mov.b32 %0, %1;" : "=r"(wj) : "r"(w[j][k]));
-                    const float2 f = Cvt16<T>::unpack(wj);
-                    float lo, hi;
-                    unpack2(pack2(f.x, f.y) + h[j], lo, hi);
-                    w[j][k] = Cvt16<T>::pack(lo, hi);
-                }
+                for (int j = 0; j < 19; ++j) w[j][k] = add_to_pair<T>(w[j][k], h[j]);
             }
 #pragma unroll
             for (int j = 0; j < 19; ++j) store_raw16<8>(dst + j * n + r00 + x0, w[j]);
