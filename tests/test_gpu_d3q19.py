@@ -71,6 +71,19 @@ def test_16bit_3d_rows_of_several_segments(storage, tol, shape):
     np.testing.assert_array_equal(outs[8], outs[4])
 
 
+@pytest.mark.parametrize("storage,tol", [("fp16", 2e-3), ("bf16", 2e-2)])
+@pytest.mark.parametrize("shape", [(8, 1, 1), (8, 3, 1), (16, 1, 3), (256, 1, 2)])
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed"])
+def test_16bit_3d_degenerate_8_node_packs(storage, tol, shape, mode):
+    """The staged 8-node-pack kernel where a row is one pack (the pack its own periodic
+    neighbour in x) or where y or z has one row (the row its own neighbour), in every
+    relaxation frame (each issues its copies in a different number of plane groups):
+    against the oracle and bit for bit against 4-node packs."""
+    outs = {w: _check(shape, mode, 9, tol=tol, seed=11, storage=storage, width=w)
+            for w in (4, 8)}
+    np.testing.assert_array_equal(outs[8], outs[4])
+
+
 @pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 5), (7, 3, 2), (2, 9, 1), (5, 1, 4)])
 def test_parity_degenerate_3d(shape):
     for mode in ("zero", "fluid", "prescribed"):
