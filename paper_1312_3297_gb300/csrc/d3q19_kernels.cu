@@ -148,14 +148,14 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
 
 // The same step for 16-bit storage with the packs held in storage form (two values per
 // register): wider packs (fewer, larger memory accesses and less per-node address and halo
-// work) at the register cost of narrow ones. PAIRS: 0 relaxes node by node, converting
-// each value on its own; 1 converts a node pair at once and relaxes its two nodes; 2
-// relaxes the pair by packed FP32 instructions (F2), as an increment added to the pair
-// held in its packed word. Registers are capped at 128 per thread (four 128-thread
-// blocks per SM). Blocks span several rows when a row has fewer
-// than 128 packs (a warp stays within one row); with the row index per thread the
-// compiler spills less than with one row per block (measured).
-template <typename T, int NV, int UM, int PAIRS, int RCP>
+// work) at the register cost of narrow ones. Each node pair is converted to FP32 just
+// before it is relaxed by packed FP32 instructions (F2), as an increment added to the pair
+// held in its packed word (measured faster than relaxing node by node or pair by pair in
+// scalar form). Registers are capped at 128 per thread (four 128-thread blocks per SM).
+// Blocks span several rows when a row has fewer than 128 packs (a warp stays within one
+// row); with the row index per thread the compiler spills less than with one row per
+// block (measured).
+template <typename T, int NV, int UM, int RCP>
 __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict__ src,
                                                          T* __restrict__ dst, StepArgs3 a) {
     pdl_wait_prior();
@@ -188,59 +188,27 @@ __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict_
             load_raw16<NV>(s + 16 * n + r.rpp + p.x0, p.act, w[16]);
             load_raw16<NV>(s + 17 * n + r.rmp + p.x0, p.act, w[17]);
             load_raw16<NV>(s + 18 * n + r.rpm + p.x0, p.act, w[18]);
-            if (p.act && PAIRS == 0) {
-#pragma unroll
-                for (int e = 0; e < NV; ++e) {
-                    float h[19];
-#pragma unroll
-                    for (int j = 0; j < 19; ++j) h[j] = Cvt16<T>::get(w[j][e / 2], e % 2);
-                    float ux = 0.0f, uy = 0.0f, uz = 0.0f;
-                    if constexpr (UM != UM_ZERO && UM != UM_FLUID)
-                        relative_velocity3<UM>(h, r.r00 + p.x0 + e, n, a, ux, uy, uz);
-                    relax_node3<UM, RCP>(h, ux, uy, uz, a.s, a.ref);
-#pragma unroll
-                    for (int j = 0; j < 19; ++j) w[j][e / 2] = Cvt16<T>::put(w[j][e / 2], e % 2, h[j]);
-                }
-            } else if (p.act) {
+            if (p.act) {
 #pragma unroll
                 for (int k = 0; k < NV / 2; ++k) {
                     const int64_t i = r.r00 + p.x0 + 2 * k;  // first node of the pair
-                    if constexpr (PAIRS == 2) {
-                        F2 h[19];
+                    F2 h[19];
 #pragma unroll
-                        for (int j = 0; j < 19; ++j) {
-                            const float2 f = Cvt16<T>::unpack(w[j][k]);
-                            h[j] = pack2(f.x, f.y);
-                        }
-                        F2 ux(0.0f), uy(0.0f), uz(0.0f);
-                        if constexpr (UM != UM_ZERO && UM != UM_FLUID) {
-                            const F2 amp(a.amp_t);
-                            ux = amp * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
-                            uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
-                            uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
-                        }
-                        relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
-#pragma unroll
-                        for (int j = 0; j < 19; ++j)  // the stored pair plus its increments
-                            w[j][k] = add_to_pair<T>(w[j][k], h[j]);
-                    } else {
-                        float h0[19], h1[19];
-#pragma unroll
-                        for (int j = 0; j < 19; ++j) {
-                            const float2 f = Cvt16<T>::unpack(w[j][k]);
-                            h0[j] = f.x;
-                            h1[j] = f.y;
-                        }
-                        float ux = 0.0f, uy = 0.0f, uz = 0.0f;
-                        if constexpr (UM != UM_ZERO && UM != UM_FLUID)
-                            relative_velocity3<UM>(h0, i, n, a, ux, uy, uz);
-                        relax_node3<UM, RCP>(h0, ux, uy, uz, a.s, a.ref);
-                        if constexpr (UM != UM_ZERO && UM != UM_FLUID)
-                            relative_velocity3<UM>(h1, i + 1, n, a, ux, uy, uz);
-                        relax_node3<UM, RCP>(h1, ux, uy, uz, a.s, a.ref);
-#pragma unroll
-                        for (int j = 0; j < 19; ++j) w[j][k] = Cvt16<T>::pack(h0[j], h1[j]);
+                    for (int j = 0; j < 19; ++j) {
+                        const float2 f = Cvt16<T>::unpack(w[j][k]);
+                        h[j] = pack2(f.x, f.y);
                     }
+                    F2 ux(0.0f), uy(0.0f), uz(0.0f);
+                    if constexpr (UM != UM_ZERO && UM != UM_FLUID) {
+                        const F2 amp(a.amp_t);
+                        ux = amp * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
+                        uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
+                        uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
+                    }
+                    relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                    for (int j = 0; j < 19; ++j)  // the stored pair plus its increments
+                        w[j][k] = add_to_pair<T>(w[j][k], h[j]);
                 }
             }
             if (p.act) {
@@ -640,14 +608,11 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// 16-bit packs of 4 and 8 nodes run in storage form (k_step3_r16), relaxed in pairs by
-// packed FP32 instructions, with the correctly rounded 1/rho (measured fastest on GB300 at
-// 256^3: 70 k MLUPS with 8-node packs against 54 k for 2-node packs converted on load).
-constexpr int kPairs3 = 2;
+// 16-bit packs of 4 and 8 nodes run in storage form, relaxed in pairs by packed FP32
+// instructions, with the correctly rounded 1/rho (measured fastest on GB300 at 256^3).
+// 8-node packs run the shared-memory pipeline (k_step3_pipe) unless ny * nz needs more
+// than 31 bits, then the register kernel (k_step3_r16).
 constexpr int kRcp3 = RCP_RN;
-
-// Whether 8-node 16-bit packs run the shared-memory pipeline (k_step3_pipe).
-constexpr bool kPipe3 = true;
 
 template <typename T, int UM>
 cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st) {
@@ -677,12 +642,12 @@ cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStr
 template <typename T, int UM>
 cudaError_t step3_nv(const void* src, void* dst, const StepArgs3& a, cudaStream_t st, int nv) {
     if constexpr (sizeof(T) == 2) {
-        if (nv == 8 && kPipe3 && (int64_t)a.ny * a.nz < (1LL << 31))
+        if (nv == 8 && (int64_t)a.ny * a.nz < (1LL << 31))
             return launch_pipe3<T, UM>(src, dst, a, st);
         if (nv == 4)
-            return launch3(k_step3_r16<T, 4, UM, kPairs3, kRcp3>, src, dst, a, st, nv, true);
+            return launch3(k_step3_r16<T, 4, UM, kRcp3>, src, dst, a, st, nv, true);
         if (nv == 8)
-            return launch3(k_step3_r16<T, 8, UM, kPairs3, kRcp3>, src, dst, a, st, nv, true);
+            return launch3(k_step3_r16<T, 8, UM, kRcp3>, src, dst, a, st, nv, true);
     } else {
         if (nv == 4) return launch3(k_step3<T, 4, UM>, src, dst, a, st, nv);
     }
