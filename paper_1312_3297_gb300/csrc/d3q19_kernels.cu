@@ -3,6 +3,7 @@
 // (z*ny + y)*nx + x.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <type_traits>
 
 #include "d3q19.cuh"
@@ -617,22 +618,33 @@ constexpr int kRcp3 = RCP_RN;
 template <typename T, int UM>
 cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st) {
     auto kernel = k_step3_pipe<T, UM, kRcp3>;
-    cudaError_t e =
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPipeSmem);
-    int dev = 0, sms = 0, per_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kPipeWarps * 32,
-                                                          kPipeSmem);
+    // Resident blocks of this kernel on each device (SMs x blocks per SM), found once per
+    // device with the shared-memory attribute set: 0 = not yet known.
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> resident[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    // persistent: no more blocks than are resident at once (work is split between warps
-    // up front)
-    per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+    int full = dev < kMaxDevices ? resident[dev].load(std::memory_order_relaxed) : 0;
+    if (full == 0) {
+        int sms = 0, per_sm = 0;
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kPipeSmem);
+        if (e == cudaSuccess)
+            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel,
+                                                              kPipeWarps * 32, kPipeSmem);
+        if (e != cudaSuccess) return e;
+        // persistent: no more blocks than are resident at once (work is split between
+        // warps up front)
+        per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+        full = per_sm * sms;
+        if (dev < kMaxDevices) resident[dev].store(full, std::memory_order_relaxed);
+    }
     const int64_t segs = (a.nx + kPipeSeg - 1) / kPipeSeg;
     const int64_t items = (int64_t)a.ny * a.nz * segs;
     const int64_t need = (items + kPipeWarps - 1) / kPipeWarps;
-    const int64_t full = (int64_t)per_sm * sms;
     const int blocks = (int)(need < full ? need : full);
     e = launch_pdl_smem(kernel, dim3(blocks), dim3(kPipeWarps * 32), kPipeSmem, st,
                         static_cast<const T*>(src), static_cast<T*>(dst), a);
