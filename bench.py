@@ -328,6 +328,7 @@ def gpu_arm(args):
                                                      big, k, peak)
             del big
             extras["cascaded_geier_fluid"] = cascaded_measure(torch, inp, fields, k, peak)
+            extras["conserved_sums_4096"] = sums_measure(torch, D2Q9, inp, fields)
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
             extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
         e2e = (e2e_measure(torch, D2Q9, inp, fields, args.steps)
@@ -363,6 +364,28 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def sums_measure(torch, D2Q9, inp, fields, reps: int = 30):
+    """One step followed by the FP64 conserved sums of its result, synchronously: with the
+    sums fused into the step kernel (lbmrv_step_conserved) and with the separate reduction
+    pass over the stored state (lbmrv_step + lbmrv_conserved3). Wall clock per check."""
+    sim = make_sim(torch, D2Q9, inp, "fp32", "prescribed", L, fields)
+    sim.step(3)
+    out = {}
+    for name, check in (("fused", lambda: sim.step_conserved(1)),
+                        ("separate", lambda: (sim.step(1), sim.conserved3()))):
+        check()
+        torch.cuda.synchronize()
+        runs = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            check()
+            runs.append((time.perf_counter() - t0) * 1e3)
+        out[f"{name}_ms"] = round(statistics.median(runs), 4)
+    sim.close()
+    out["saved_ms"] = round(out["separate_ms"] - out["fused_ms"], 4)
+    return out
 
 
 def cascaded_measure(torch, inp, fields, steps, peak):

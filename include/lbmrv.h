@@ -204,6 +204,18 @@ LBMRV_API int lbmrv_conserved(lbmrv_t h, double out_host[4]);
  * sum q_y, sum q_z (0 for D2Q9), non-finite nodes}. */
 LBMRV_API int lbmrv_conserved3(lbmrv_t h, double out_host[5]);
 
+/* n >= 1 steps (as lbmrv_step), then the sums of lbmrv_conserved3 of the resulting state,
+ * taken inside the last step's kernel from the values it stores (rounded to the storage
+ * type), so the state is not read a second time (relation (rhoq) summed over the
+ * lattice). D2Q9 with a vector kernel width (nodes per thread >= 2); other lattices and
+ * widths run the step, then lbmrv_conserved3's own pass. The sums are added in a fixed
+ * order (deterministic for a given width); they agree with lbmrv_conserved3 of the same
+ * state to FP64 rounding of FP32 node moments. The first call, and a call after the
+ * lattice or width changed, allocates about 32 bytes per step-kernel block of scratch,
+ * kept until lbmrv_destroy. Synchronous. Returns LBMRV_E_NONFINITE (after filling
+ * out_host) when non-finite nodes were found, LBMRV_E_INVAL for n < 1. */
+LBMRV_API int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]);
+
 /* Copy the current stored state (layout above) to / from a device buffer of
  * lbmrv_state_bytes(). set_state also sets the time index to t. */
 LBMRV_API int lbmrv_get_state(lbmrv_t h, void* dst_dev);

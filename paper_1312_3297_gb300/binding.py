@@ -67,6 +67,7 @@ SIGNATURES = [
     ("lbmrv_set_rates", _I, [_VP, _DP]),
     ("lbmrv_set_reference", _I, [_VP, _D, _DP]),
     ("lbmrv_conserved3", _I, [_VP, _DP]),
+    ("lbmrv_step_conserved", _I, [_VP, _I64, _DP]),
     ("lbmrv_adjoint_workspace_bytes", _I64, [_VP, _I64, _I64]),
     ("lbmrv_forward_checkpointed", _I, [_VP, _I64, _I64, _VP, ctypes.c_size_t]),
     ("lbmrv_adjoint", _I, [_VP, _I64, _I64, _VP, ctypes.c_size_t, _VP, _VP, _DP, _DP, _VP]),
@@ -247,6 +248,15 @@ def lbmrv_set_reference(h, rho_ref: float, u_ref) -> None:
 def lbmrv_conserved3(h, allow_nonfinite: bool = False):
     out = (ctypes.c_double * 5)()
     rc = load().lbmrv_conserved3(h, out)
+    if rc == LBMRV_E_NONFINITE and allow_nonfinite:
+        return list(out)
+    _check(rc, h)
+    return list(out)
+
+
+def lbmrv_step_conserved(h, n: int, allow_nonfinite: bool = False):
+    out = (ctypes.c_double * 5)()
+    rc = load().lbmrv_step_conserved(h, int(n), out)
     if rc == LBMRV_E_NONFINITE and allow_nonfinite:
         return list(out)
     _check(rc, h)

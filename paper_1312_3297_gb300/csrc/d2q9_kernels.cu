@@ -45,6 +45,37 @@ constexpr int paired_rcp() {
     return UM == UM_ZERO ? RCP_RN : RCP_DIV;
 }
 
+// --------------------------------------------------------------------------------------
+// FP64 sums of the deviations (sum g, sum c g, non-finite nodes): per-node
+// FP32 moments accumulated in FP64 per thread, warp-shuffle and shared-memory tree per
+// block, one partial per block; a second one-block kernel adds the partials in a fixed
+// order, so the result is deterministic.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
+    return v;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_sum4(double v[4], double* out) {
+    __shared__ double sh[NT / 32][4];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        v[c] = warp_sum(v[c]);
+        if (l == 0) sh[w][c] = v[c];
+    }
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            double t = l < NT / 32 ? sh[l][c] : 0.0;
+            t = warp_sum(t);
+            if (l == 0) out[c] = t;
+        }
+    }
+}
+
 template <typename T, int UM, int BASIS>
 __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
                                                      T* __restrict__ dst, StepArgs a) {
@@ -82,14 +113,21 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 // --------------------------------------------------------------------------------------
 // Fused step, NV consecutive nodes of a row per thread with aligned vector loads and
 // stores (requires nx % NV == 0 and 16-byte aligned planes); row loads in pull.cuh.
-template <typename T, int NV, int UM, int BASIS>
+//
+// SUMS: also add up the conserved moments of the stored result (the values as rounded to
+// the storage type) in the block's slot part[4 * block] (sum g, sum c_x g, sum c_y g,
+// non-finite nodes), as k_conserved_partial does for a stored state; k_conserved_final then
+// adds the slots in a fixed order.
+template <typename T, int NV, int UM, int BASIS, bool SUMS = false>
 __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
-                                                  T* __restrict__ dst, StepArgs a) {
+                                                  T* __restrict__ dst, StepArgs a,
+                                                  double* __restrict__ part) {
     pdl_wait_prior();
     pdl_allow_next();
     const int nx = a.nx, ny = a.ny;
     const int64_t n = (int64_t)nx * ny;
     const PackLane p = pack_lane<NV>(nx);
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};
     for (int y = blockIdx.y; y < ny; y += gridDim.y) {
         const int ym = y == 0 ? ny - 1 : y - 1;
         const int yp = y == ny - 1 ? 0 : y + 1;
@@ -147,8 +185,28 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
             }
 #pragma unroll
             for (int j = 0; j < 9; ++j) store_pack<T, NV>(dst + j * n + r0 + p.x0, g[j]);
+            if constexpr (SUMS) {
+                float r[3] = {0.f, 0.f, 0.f};  // NV <= 8 node moments in FP32, then FP64
+                int bad = 0;
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    float h[9];
+#pragma unroll
+                    for (int j = 0; j < 9; ++j) h[j] = to_f(from_f<T>(g[j][k]));
+                    const NodeMoments m = node_moments(h);
+                    r[0] += m.drho;
+                    r[1] += m.jx;
+                    r[2] += m.jy;
+                    bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy)) ? 0 : 1;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c) sums[c] += (double)r[c];
+                sums[3] += (double)bad;
+            }
         }
     }
+    if constexpr (SUMS)
+        block_sum4<128>(sums, part + 4 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
 }
 
 // --------------------------------------------------------------------------------------
@@ -225,37 +283,6 @@ __global__ void k_moments(const T* __restrict__ src, float* __restrict__ rho,
     }
 }
 
-// --------------------------------------------------------------------------------------
-// FP64 sums of the deviations (sum g, sum c g, non-finite nodes): per-node
-// FP32 moments accumulated in FP64 per thread, warp-shuffle and shared-memory tree per
-// block, one partial per block; a second one-block kernel adds the partials in a fixed
-// order, so the result is deterministic.
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFullMask, v, o);
-    return v;
-}
-
-template <int NT>
-__device__ __forceinline__ void block_sum4(double v[4], double* out) {
-    __shared__ double sh[NT / 32][4];
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        v[c] = warp_sum(v[c]);
-        if (l == 0) sh[w][c] = v[c];
-    }
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            double t = l < NT / 32 ? sh[l][c] : 0.0;
-            t = warp_sum(t);
-            if (l == 0) out[c] = t;
-        }
-    }
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* __restrict__ src,
                                                                       int64_t n,
@@ -312,33 +339,53 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_final(const double
     }
 }
 
+// Block b adds partials [256 b, 256 b + 256) of 4 doubles each into out[4 b].
+__global__ void __launch_bounds__(kReduceThreads) k_sum_partials(const double* __restrict__ part,
+                                                                 int64_t nblk,
+                                                                 double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * kReduceThreads + threadIdx.x;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    if (i < nblk) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = part[4 * i + c];
+    }
+    block_sum4<kReduceThreads>(v, out + 4 * (int64_t)blockIdx.x);
+}
+
 int grid_for(int64_t n, int threads) {
     int64_t b = (n + threads - 1) / threads;
     const int64_t cap = 152LL * 16;
     return (int)(b < 1 ? 1 : (b > cap ? cap : b));
 }
 
+template <typename T, int NV, int UM, int BASIS>
+cudaError_t launch_vec(const T* s, T* d, const StepArgs& a, cudaStream_t st, double* part) {
+    const dim3 grid(((a.nx / NV) + 127) / 128, a.ny < 65535 ? a.ny : 65535);
+    // successive steps overlap their launch with the previous step's tail (pdl.cuh)
+    return part ? launch_pdl(k_step_vec<T, NV, UM, BASIS, true>, grid, dim3(128), st, s, d, a,
+                             part)
+                : launch_pdl(k_step_vec<T, NV, UM, BASIS, false>, grid, dim3(128), st, s, d, a,
+                             static_cast<double*>(nullptr));
+}
+
 template <typename T, int UM, int BASIS>
 cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
-                             int nv) {
+                             int nv, double* part) {
     const T* s = static_cast<const T*>(src);
     T* d = static_cast<T*>(dst);
     const int gy = a.ny < 65535 ? a.ny : 65535;
-    // successive steps overlap their launch with the previous step's tail (pdl.cuh)
     cudaError_t e;
     if (nv == 1) {
+        if (part) return cudaErrorInvalidValue;  // sums are fused into the vector kernel only
         e = launch_pdl(k_step_scalar<T, UM, BASIS>, dim3((a.nx + 255) / 256, gy), dim3(256), st,
                        s, d, a);
     } else if (nv == 2) {
-        e = launch_pdl(k_step_vec<T, 2, UM, BASIS>, dim3(((a.nx / 2) + 127) / 128, gy),
-                       dim3(128), st, s, d, a);
+        e = launch_vec<T, 2, UM, BASIS>(s, d, a, st, part);
     } else if (nv == 4) {
-        e = launch_pdl(k_step_vec<T, 4, UM, BASIS>, dim3(((a.nx / 4) + 127) / 128, gy),
-                       dim3(128), st, s, d, a);
+        e = launch_vec<T, 4, UM, BASIS>(s, d, a, st, part);
     } else if (nv == 8) {
         if constexpr (sizeof(T) == 2) {
-            e = launch_pdl(k_step_vec<T, 8, UM, BASIS>, dim3(((a.nx / 8) + 127) / 128, gy),
-                           dim3(128), st, s, d, a);
+            e = launch_vec<T, 8, UM, BASIS>(s, d, a, st, part);
         } else {
             return cudaErrorInvalidValue;
         }
@@ -350,21 +397,22 @@ cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cuda
 
 template <typename T, int BASIS>
 cudaError_t step_dispatch_um(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
-                             int um, int nv) {
+                             int um, int nv, double* part) {
     switch (um) {
-        case UM_ZERO: return step_dispatch_nv<T, UM_ZERO, BASIS>(src, dst, a, st, nv);
-        case UM_FLUID: return step_dispatch_nv<T, UM_FLUID, BASIS>(src, dst, a, st, nv);
-        case UM_ANALYTIC: return step_dispatch_nv<T, UM_ANALYTIC, BASIS>(src, dst, a, st, nv);
-        case UM_FIELD: return step_dispatch_nv<T, UM_FIELD, BASIS>(src, dst, a, st, nv);
+        case UM_ZERO: return step_dispatch_nv<T, UM_ZERO, BASIS>(src, dst, a, st, nv, part);
+        case UM_FLUID: return step_dispatch_nv<T, UM_FLUID, BASIS>(src, dst, a, st, nv, part);
+        case UM_ANALYTIC:
+            return step_dispatch_nv<T, UM_ANALYTIC, BASIS>(src, dst, a, st, nv, part);
+        case UM_FIELD: return step_dispatch_nv<T, UM_FIELD, BASIS>(src, dst, a, st, nv, part);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
 cudaError_t step_dispatch_basis(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
-                                int um, int nv, int basis) {
-    return basis == 0 ? step_dispatch_um<T, 0>(src, dst, a, st, um, nv)
-                      : step_dispatch_um<T, 1>(src, dst, a, st, um, nv);
+                                int um, int nv, int basis, double* part) {
+    return basis == 0 ? step_dispatch_um<T, 0>(src, dst, a, st, um, nv, part)
+                      : step_dispatch_um<T, 1>(src, dst, a, st, um, nv, part);
 }
 
 }  // namespace
@@ -379,15 +427,54 @@ int step_vector_width(int storage, int nx) {
     return 1;
 }
 
-cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
-                        const StepArgs& a, cudaStream_t st, int basis) {
+namespace {
+
+cudaError_t step_storage(int storage, int um, int nv, const void* src, void* dst,
+                         const StepArgs& a, cudaStream_t st, int basis, double* part) {
     switch (storage) {
-        case kStoreF32: return step_dispatch_basis<float>(src, dst, a, st, um, nv, basis);
-        case kStoreF16: return step_dispatch_basis<__half>(src, dst, a, st, um, nv, basis);
+        case kStoreF32: return step_dispatch_basis<float>(src, dst, a, st, um, nv, basis, part);
+        case kStoreF16:
+            return step_dispatch_basis<__half>(src, dst, a, st, um, nv, basis, part);
         case kStoreBF16:
-            return step_dispatch_basis<__nv_bfloat16>(src, dst, a, st, um, nv, basis);
+            return step_dispatch_basis<__nv_bfloat16>(src, dst, a, st, um, nv, basis, part);
         default: return cudaErrorInvalidValue;
     }
+}
+
+}  // namespace
+
+cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
+                        const StepArgs& a, cudaStream_t st, int basis) {
+    return step_storage(storage, um, nv, src, dst, a, st, basis, nullptr);
+}
+
+int64_t step_sum_blocks(int nx, int ny, int nv) {
+    return (int64_t)(((nx / nv) + 127) / 128) * (ny < 65535 ? ny : 65535);
+}
+
+int64_t step_sum_scratch(int nx, int ny, int nv) {
+    const int64_t nblk = step_sum_blocks(nx, ny, nv);
+    return 4 * nblk + 4 * ((nblk + kReduceThreads - 1) / kReduceThreads);
+}
+
+cudaError_t launch_step_conserved(int storage, int um, int nv, const void* src, void* dst,
+                                  const StepArgs& a, cudaStream_t st, int basis, double rho_ref,
+                                  double jx_ref, double jy_ref, double lambda,
+                                  double* partials, double* out) {
+    if (nv < 2 || !partials || !out) return cudaErrorInvalidValue;
+    cudaError_t e = step_storage(storage, um, nv, src, dst, a, st, basis, partials);
+    if (e != cudaSuccess) return e;
+    // the step's block partials, a fixed 256 per block of a middle level, then one block
+    const int64_t nblk = step_sum_blocks(a.nx, a.ny, nv);
+    const int64_t mid = (nblk + kReduceThreads - 1) / kReduceThreads;
+    double* mids = partials + 4 * nblk;
+    k_sum_partials<<<(unsigned)mid, kReduceThreads, 0, st>>>(partials, nblk, mids);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double n = (double)a.nx * (double)a.ny;
+    k_conserved_final<<<1, kReduceThreads, 0, st>>>(mids, (int)mid, rho_ref * n, jx_ref * n,
+                                                    jy_ref * n, lambda, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,

@@ -34,6 +34,8 @@ struct lbmrv_s {
     double amp = 0.0, period = 0.0;
     double* red = nullptr;   // reduction scratch: 8 * red_blocks partials + 8 results
     int red_blocks = 0;
+    double* fused = nullptr;  // partials of the step with fused sums, + 4 results (lazy)
+    int64_t fused_doubles = 0;
     float* sin_x = nullptr;  // sin(2 pi x / nx) table of the analytic prescribed field
     // last lbmrv_forward_checkpointed: the adjoint must match it
     bool ckpt_valid = false;

@@ -23,6 +23,15 @@ int step_vector_width(int storage, int nx);
 cudaError_t launch_step(int storage, int um, int nv, const void* src, void* dst,
                         const StepArgs& a, cudaStream_t st, int basis = 0);
 
+// The same step (nv >= 2) with the FP64 conserved sums of dst fused in, written to out[4]
+// as launch_conserved does; partials: step_sum_scratch(nx, ny, nv) doubles of scratch.
+int64_t step_sum_blocks(int nx, int ny, int nv);
+int64_t step_sum_scratch(int nx, int ny, int nv);
+cudaError_t launch_step_conserved(int storage, int um, int nv, const void* src, void* dst,
+                                  const StepArgs& a, cudaStream_t st, int basis, double rho_ref,
+                                  double jx_ref, double jy_ref, double lambda,
+                                  double* partials, double* out);
+
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
                            const StoreRef& ref, float inv_lambda, cudaStream_t st,
                            int basis = 0);

@@ -186,6 +186,7 @@ int lbmrv_destroy(lbmrv_t h) {
     }
     cudaFree(h->red);
     cudaFree(h->sin_x);
+    cudaFree(h->fused);
     delete h;
     return LBMRV_OK;
 }
@@ -369,6 +370,57 @@ int lbmrv_conserved3(lbmrv_t h, double out_host[5]) {
     if (out_host[4] > 0.0)
         return fail(h, LBMRV_E_NONFINITE, "lbmrv_conserved: %.0f nodes hold non-finite values",
                     out_host[4]);
+    return LBMRV_OK;
+}
+
+int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]) {
+    lbmrv::TraceRange trace("lbmrv_step_conserved");
+    if (!h || !out_host) return fail(h, LBMRV_E_INVAL, "lbmrv_step_conserved: NULL argument");
+    if (n < 1) return fail(h, LBMRV_E_INVAL, "lbmrv_step_conserved: n < 1");
+    int rc = lbmrv_step(h, n - 1);
+    if (rc != LBMRV_OK) return rc;
+    DeviceGuard g(h->device);
+    const int nv = choose_width(h, h->f[0], h->f[1]);
+    if (h->dim != 2 || nv < 2) {  // no fused form: the step, then the sums' own pass
+        rc = lbmrv_step(h, 1);
+        return rc != LBMRV_OK ? rc : lbmrv_conserved3(h, out_host);
+    }
+    const int64_t need = step_sum_scratch((int)h->nx, (int)h->ny, nv) + 4;
+    if (need > h->fused_doubles) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);  // the old scratch may be in use
+        if (e == cudaSuccess) e = cudaFree(h->fused);
+        h->fused = nullptr;
+        h->fused_doubles = 0;
+        if (e == cudaSuccess)
+            e = cudaMalloc(reinterpret_cast<void**>(&h->fused), sizeof(double) * need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->fused = nullptr;
+            return fail(h, LBMRV_E_NOMEM, "lbmrv_step_conserved: scratch of %lld doubles: %s",
+                        (long long)need, cudaGetErrorString(e));
+        }
+        h->fused_doubles = need;
+    }
+    double* res = h->fused + (need - 4);
+    cudaError_t e = launch_step_conserved(
+        h->storage, kernel_mode(h), nv, h->f[h->cur], h->f[1 - h->cur], make_args(h, h->t + 1),
+        h->stream, h->basis, h->rho_ref, h->rho_ref * h->u_ref[0] / h->lambda,
+        h->rho_ref * h->u_ref[1] / h->lambda, h->lambda, h->fused, res);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_step_conserved");
+    h->cur = 1 - h->cur;
+    h->t += 1;
+    double four[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(four, res, sizeof(four), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_step_conserved");
+    out_host[0] = four[0];
+    out_host[1] = four[1];
+    out_host[2] = four[2];
+    out_host[3] = 0.0;
+    out_host[4] = four[3];
+    if (out_host[4] > 0.0)
+        return fail(h, LBMRV_E_NONFINITE,
+                    "lbmrv_step_conserved: %.0f nodes hold non-finite values", out_host[4]);
     return LBMRV_OK;
 }
 

@@ -164,6 +164,11 @@ class D2Q9:
         """[sum rho, sum q_x, sum q_y, sum q_z, non-finite nodes]."""
         return B.lbmrv_conserved3(self.h, allow_nonfinite=allow_nonfinite)
 
+    def step_conserved(self, n: int = 1, allow_nonfinite: bool = False):
+        """n steps, the last with the sums of conserved3() of its result taken in the same
+        kernel (D2Q9 vector widths; otherwise a separate pass)."""
+        return B.lbmrv_step_conserved(self.h, n, allow_nonfinite=allow_nonfinite)
+
     def state(self) -> torch.Tensor:
         """Copy of the stored state g = f - f_eq(rho_ref, u_ref), shape (9, ny, nx), in the
         storage dtype."""
