@@ -612,7 +612,8 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 // 16-bit packs of 4 and 8 nodes run in storage form, relaxed in pairs by packed FP32
 // instructions, with the correctly rounded 1/rho (measured fastest on GB300 at 256^3).
 // 8-node packs run the shared-memory pipeline (k_step3_pipe) unless ny * nz needs more
-// than 31 bits, then the register kernel (k_step3_r16).
+// than 31 bits; then, and for 4-node packs, the register kernel (k_step3_r16) runs 4-node
+// packs.
 constexpr int kRcp3 = RCP_RN;
 
 template <typename T, int UM>
@@ -656,10 +657,8 @@ cudaError_t step3_nv(const void* src, void* dst, const StepArgs3& a, cudaStream_
     if constexpr (sizeof(T) == 2) {
         if (nv == 8 && (int64_t)a.ny * a.nz < (1LL << 31))
             return launch_pipe3<T, UM>(src, dst, a, st);
-        if (nv == 4)
-            return launch3(k_step3_r16<T, 4, UM, kRcp3>, src, dst, a, st, nv, true);
-        if (nv == 8)
-            return launch3(k_step3_r16<T, 8, UM, kRcp3>, src, dst, a, st, nv, true);
+        if (nv == 4 || nv == 8)  // (8-node packs with ny * nz >= 2^31: 4-node packs)
+            return launch3(k_step3_r16<T, 4, UM, kRcp3>, src, dst, a, st, 4, true);
     } else {
         if (nv == 4) return launch3(k_step3<T, 4, UM>, src, dst, a, st, nv);
     }
