@@ -103,11 +103,14 @@ def test_null_handle_calls_fail_cleanly():
                      (B.lbmrv_set_utilde, (None, None, 0.0, 0.0)),
                      (B.lbmrv_init_equilibrium, (None, None, None)),
                      (B.lbmrv_moments, (None, None, None)),
-                     (B.lbmrv_set_kernel_width, (None, 1))]:
+                     (B.lbmrv_set_kernel_width, (None, 1)),
+                     (B.lbmrv_step_conserved, (None, 1)), (B.lbmrv_conserved3, (None,))]:
         with pytest.raises(B.LbmrvError) as ei:
             fn(*args)
         assert ei.value.status == B.LBMRV_E_INVAL
     assert B.lbmrv_time(None) == -1
+    # a NULL output array is rejected before the handle is used
+    assert B.load().lbmrv_step_conserved(None, 1, None) == B.LBMRV_E_INVAL
     B.lbmrv_destroy(None)
 
 
