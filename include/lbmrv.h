@@ -207,11 +207,12 @@ LBMRV_API int lbmrv_conserved3(lbmrv_t h, double out_host[5]);
 /* n >= 1 steps (as lbmrv_step), then the sums of lbmrv_conserved3 of the resulting state,
  * taken inside the last step's kernel from the values it stores (rounded to the storage
  * type), so the state is not read a second time (relation (rhoq) summed over the
- * lattice). D2Q9 with a vector kernel width (nodes per thread >= 2); other lattices and
- * widths run the step, then lbmrv_conserved3's own pass. The sums are added in a fixed
+ * lattice). Fused for D2Q9 at vector kernel widths (nodes per thread >= 2) and for D3Q19
+ * at its default widths (FP32: 4 nodes per thread; FP16/BF16: 8); other widths run the
+ * step, then lbmrv_conserved3's own pass. The sums are added in a fixed
  * order (deterministic for a given width); they agree with lbmrv_conserved3 of the same
  * state to FP64 rounding of FP32 node moments. The first call, and a call after the
- * lattice or width changed, allocates about 32 bytes per step-kernel block of scratch,
+ * lattice or width changed, allocates 32-64 bytes per step-kernel block of scratch,
  * kept until lbmrv_destroy. Synchronous. Returns LBMRV_E_NONFINITE (after filling
  * out_host) when non-finite nodes were found, LBMRV_E_INVAL for n < 1. */
 LBMRV_API int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]);

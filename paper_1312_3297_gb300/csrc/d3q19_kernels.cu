@@ -21,7 +21,7 @@ constexpr int kThreads3 = 128;
 template <typename K>
 struct KernelArg;
 template <typename T>
-struct KernelArg<void (*)(const T*, T*, StepArgs3)> {
+struct KernelArg<void (*)(const T*, T*, StepArgs3, double*)> {
     using type = T;
 };
 
@@ -88,6 +88,42 @@ __device__ __forceinline__ uint32_t add_to_pair(uint32_t w, F2 inc) {
     return Cvt16<T>::pack(MixedAdd<T>::add(lo, a), MixedAdd<T>::add(hi, b));
 }
 
+// Conserved moments of one stored node (values as rounded to the storage type) added to
+// r[0..3] (sum g, sum c g), and its non-finite flag to bad.
+template <typename T>
+__device__ __forceinline__ void add_node_sums3(const float g[19], float r[4], int& bad) {
+    float h[19];
+#pragma unroll
+    for (int j = 0; j < 19; ++j) h[j] = to_f(from_f<T>(g[j]));
+    const NodeMoments3 m = node_moments3(h);
+    r[0] += m.drho;
+    r[1] += m.jx;
+    r[2] += m.jy;
+    r[3] += m.jz;
+    bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy) && isfinite(m.jz)) ? 0 : 1;
+}
+
+// Sums of v[0..4] over the block (a multiple of 32 threads, at most 1024) into
+// slot[0..4]; every thread of the block must call it.
+__device__ __forceinline__ void block_sum5(const double v[5], double* __restrict__ slot) {
+    __shared__ double sh[32][5];
+    const int t = threadIdx.x + blockDim.x * threadIdx.y;
+    const int nw = (blockDim.x * blockDim.y) >> 5, w = t >> 5, l = t & 31;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+        double x = v[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(kFullMask, x, o);
+        if (l == 0) sh[w][c] = x;
+    }
+    __syncthreads();
+    if (t < 5) {
+        double x = 0.0;
+        for (int k = 0; k < nw; ++k) x += sh[k][t];
+        slot[t] = x;
+    }
+}
+
 // Thread blocks of 32 to kThreads3 threads (a multiple of 32) along one row, each thread
 // owning NV consecutive nodes, sized to the row so that short rows leave no warp idle; the
 // row index stays uniform across the block (its offsets are computed once per warp, in
@@ -95,14 +131,20 @@ __device__ __forceinline__ uint32_t add_to_pair(uint32_t w, F2 inc) {
 //
 // One thread: NV consecutive nodes of the row (y, z). Population j is pulled from
 // (x, y, z) - c_j, periodic (relation (transport)).
-template <typename T, int NV, int UM>
+//
+// SUMS: also add up the conserved moments of the stored result in the block's slot
+// part[8 * block] (sum g, sum c g, non-finite nodes), as k_conserved3_partial does for a
+// stored state.
+template <typename T, int NV, int UM, bool SUMS = false>
 __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
-                                                     T* __restrict__ dst, StepArgs3 a) {
+                                                     T* __restrict__ dst, StepArgs3 a,
+                                                     double* __restrict__ part) {
     pdl_wait_prior();
     pdl_allow_next();
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n = (int64_t)nx * ny * nz;
     const PackLane p = pack_lane<NV>(nx);
+    double sums[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     for (int z = blockIdx.z; z < nz; z += gridDim.z) {
         for (int y = blockIdx.y; y < ny; y += gridDim.y) {
             const Rows3 r(y, z, nx, ny, nz);
@@ -142,9 +184,26 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
                 }
 #pragma unroll
                 for (int j = 0; j < 19; ++j) store_pack<T, NV>(dst + j * n + r.r00 + p.x0, g[j]);
+                if constexpr (SUMS) {
+                    float rs[4] = {0.f, 0.f, 0.f, 0.f};  // NV nodes in FP32, then FP64
+                    int bad = 0;
+#pragma unroll
+                    for (int k = 0; k < NV; ++k) {
+                        float h[19];
+#pragma unroll
+                        for (int j = 0; j < 19; ++j) h[j] = g[j][k];
+                        add_node_sums3<T>(h, rs, bad);
+                    }
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) sums[c] += (double)rs[c];
+                    sums[4] += (double)bad;
+                }
             }
         }
     }
+    if constexpr (SUMS)
+        block_sum5(sums, part + 8 * (((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x +
+                                     blockIdx.x));
 }
 
 // The same step for 16-bit storage with the packs held in storage form (two values per
@@ -158,7 +217,8 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
 // block (measured).
 template <typename T, int NV, int UM, int RCP>
 __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict__ src,
-                                                         T* __restrict__ dst, StepArgs3 a) {
+                                                         T* __restrict__ dst, StepArgs3 a,
+                                                         double* /* no sums */) {
     pdl_wait_prior();
     pdl_allow_next();
     static_assert(sizeof(T) == 2 && NV >= 4 && NV % 2 == 0, "16-bit packs of 4 or more");
@@ -303,11 +363,13 @@ constexpr int pipe_plane_groups() {
     return UM == UM_ZERO ? 4 : std::is_same<T, __nv_bfloat16>::value ? 2 : 1;
 }
 
-template <typename T, int UM, int RCP>
+template <typename T, int UM, int RCP, bool SUMS = false>
 __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __restrict__ src,
                                                                    T* __restrict__ dst,
-                                                                   StepArgs3 a) {
+                                                                   StepArgs3 a,
+                                                                   double* __restrict__ part) {
     constexpr int S = kPipeStages;
+    double sums[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // SUMS: the stored result's moments
     pdl_wait_prior();
     pdl_allow_next();
     extern __shared__ __align__(16) unsigned char pipe_smem[];
@@ -447,6 +509,25 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
             }
 #pragma unroll
             for (int j = 0; j < 19; ++j) store_raw16<8>(dst + j * n + r00 + x0, w[j]);
+            if constexpr (SUMS) {
+                float rs[4] = {0.f, 0.f, 0.f, 0.f};  // 8 nodes in FP32, then FP64
+                int bad = 0;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float lo[19], hi[19];
+#pragma unroll
+                    for (int j = 0; j < 19; ++j) {
+                        const float2 f = Cvt16<T>::unpack(w[j][k]);
+                        lo[j] = f.x;
+                        hi[j] = f.y;
+                    }
+                    add_node_sums3<float>(lo, rs, bad);
+                    add_node_sums3<float>(hi, rs, bad);
+                }
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sums[c] += (double)rs[c];
+                sums[4] += (double)bad;
+            }
         } else if constexpr (Q > 1) {
 #pragma unroll
             for (int k = 1; k < 4; ++k) issue_groups_before(k);  // as the relaxation would
@@ -458,6 +539,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
         cur = advance(cur);
         stage = stage == S - 1 ? 0 : stage + 1;
     }
+    if constexpr (SUMS) block_sum5(sums, part + 8 * (int64_t)blockIdx.x);
 }
 
 __constant__ int kC3X[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -596,16 +678,20 @@ inline dim3 step3_block(int nx, int nv, bool multi_row) {
     return dim3(tx, multi_row ? kThreads3 / tx : 1, 1);
 }
 
-template <typename K>
-cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
-                    int nv, bool multi_row = false) {
+dim3 step3_grid(const StepArgs3& a, int nv, bool multi_row) {
     const dim3 b = step3_block(a.nx, nv, multi_row);
     const int packs = (a.nx + nv - 1) / nv;
     const int gy = (a.ny + (int)b.y - 1) / (int)b.y;
-    const dim3 grid((packs + b.x - 1) / b.x, gy < 65535 ? gy : 65535, a.nz < 65535 ? a.nz : 65535);
+    return dim3((packs + b.x - 1) / b.x, gy < 65535 ? gy : 65535, a.nz < 65535 ? a.nz : 65535);
+}
+
+template <typename K>
+cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                    int nv, bool multi_row = false, double* part = nullptr) {
+    const dim3 b = step3_block(a.nx, nv, multi_row);
     using TT = typename KernelArg<K>::type;
-    const cudaError_t e =
-        launch_pdl(kernel, grid, b, st, static_cast<const TT*>(src), static_cast<TT*>(dst), a);
+    const cudaError_t e = launch_pdl(kernel, step3_grid(a, nv, multi_row), b, st,
+                                     static_cast<const TT*>(src), static_cast<TT*>(dst), a, part);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -616,9 +702,10 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 // packs.
 constexpr int kRcp3 = RCP_RN;
 
-template <typename T, int UM>
-cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st) {
-    auto kernel = k_step3_pipe<T, UM, kRcp3>;
+template <typename T, int UM, bool SUMS = false>
+cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                         double* part = nullptr, int64_t* slots = nullptr) {
+    auto kernel = k_step3_pipe<T, UM, kRcp3, SUMS>;
     // Resident blocks of this kernel on each device (SMs x blocks per SM), found once per
     // device with the shared-memory attribute set: 0 = not yet known.
     constexpr int kMaxDevices = 64;
@@ -647,9 +734,28 @@ cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStr
     const int64_t items = (int64_t)a.ny * a.nz * segs;
     const int64_t need = (items + kPipeWarps - 1) / kPipeWarps;
     const int blocks = (int)(need < full ? need : full);
+    if (slots) *slots = blocks;
     e = launch_pdl_smem(kernel, dim3(blocks), dim3(kPipeWarps * 32), kPipeSmem, st,
-                        static_cast<const T*>(src), static_cast<T*>(dst), a);
+                        static_cast<const T*>(src), static_cast<T*>(dst), a, part);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// The step with the conserved sums fused in: the FP32 4-node kernel or the 16-bit
+// pipeline; *slots receives the number of block slots written.
+template <typename T, int UM>
+cudaError_t step3_sums(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                       int nv, double* part, int64_t* slots) {
+    if constexpr (sizeof(T) == 2) {
+        if (nv == 8 && (int64_t)a.ny * a.nz < (1LL << 31))
+            return launch_pipe3<T, UM, true>(src, dst, a, st, part, slots);
+    } else {
+        if (nv == 4) {
+            const dim3 g = step3_grid(a, 4, false);
+            *slots = (int64_t)g.x * g.y * g.z;
+            return launch3(k_step3<T, 4, UM, true>, src, dst, a, st, 4, false, part);
+        }
+    }
+    return cudaErrorNotSupported;
 }
 
 template <typename T, int UM>
@@ -678,7 +784,79 @@ cudaError_t step3_um(const void* src, void* dst, const StepArgs3& a, cudaStream_
     }
 }
 
+template <typename T>
+cudaError_t step3_sums_um(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                          int um, int nv, double* part, int64_t* slots) {
+    switch (um) {
+        case UM_ZERO: return step3_sums<T, UM_ZERO>(src, dst, a, st, nv, part, slots);
+        case UM_FLUID: return step3_sums<T, UM_FLUID>(src, dst, a, st, nv, part, slots);
+        case UM_FIELD: return step3_sums<T, UM_FIELD>(src, dst, a, st, nv, part, slots);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// Block b adds slots [256 b, 256 b + 256) (8 doubles each, 5 used) into out[8 b].
+__global__ void __launch_bounds__(kReduceThreads) k_sum_slots5(const double* __restrict__ part,
+                                                               int64_t nslots,
+                                                               double* __restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * kReduceThreads + threadIdx.x;
+    double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (i < nslots) {
+#pragma unroll
+        for (int c = 0; c < 5; ++c) v[c] = part[8 * i + c];
+    }
+    block_sum5(v, out + 8 * (int64_t)blockIdx.x);
+}
+
 }  // namespace
+
+bool step3_fuses_sums(int storage, int nv, int ny, int nz) {
+    return storage == kStoreF32 ? nv == 4 : nv == 8 && (int64_t)ny * nz < (1LL << 31);
+}
+
+int64_t step3_sum_scratch(int storage, int nv, const StepArgs3& a) {
+    int64_t slots = 0;
+    if (storage == kStoreF32) {
+        const dim3 g = step3_grid(a, nv, false);
+        slots = (int64_t)g.x * g.y * g.z;
+    } else {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return -1;
+        slots = 2LL * sms;  // the pipeline's persistent grid: at most 2 blocks per SM
+    }
+    return 8 * slots + 8 * ((slots + kReduceThreads - 1) / kReduceThreads);
+}
+
+cudaError_t launch_step3_conserved(int storage, int um, int nv, const void* src, void* dst,
+                                   const StepArgs3& a, cudaStream_t st, double lambda,
+                                   double* partials, int64_t scratch, double* out) {
+    if (!partials || !out || !step3_fuses_sums(storage, nv, a.ny, a.nz))
+        return cudaErrorInvalidValue;
+    int64_t slots = 0;
+    cudaError_t e;
+    switch (storage) {
+        case kStoreF32: e = step3_sums_um<float>(src, dst, a, st, um, nv, partials, &slots); break;
+        case kStoreF16: e = step3_sums_um<__half>(src, dst, a, st, um, nv, partials, &slots); break;
+        case kStoreBF16:
+            e = step3_sums_um<__nv_bfloat16>(src, dst, a, st, um, nv, partials, &slots);
+            break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    const int64_t mid = (slots + kReduceThreads - 1) / kReduceThreads;
+    if (8 * slots + 8 * mid > scratch) return cudaErrorInvalidValue;  // cannot happen
+    double* mids = partials + 8 * slots;
+    k_sum_slots5<<<(unsigned)mid, kReduceThreads, 0, st>>>(partials, slots, mids);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const double dn = (double)a.nx * (double)a.ny * (double)a.nz;
+    k_conserved3_final<<<1, 256, 0, st>>>(mids, (int)mid, (double)a.ref.rho * dn,
+                                          (double)a.ref.jx * dn, (double)a.ref.jy * dn,
+                                          (double)a.ref.jz * dn, lambda, out);
+    return cudaGetLastError();
+}
 
 int step3_vector_width(int storage, int nx) {
     // Measured fastest on GB300 at 256^3: 4-node packs for FP32, 8-node packs for 16-bit.

@@ -55,6 +55,14 @@ cudaError_t launch_init_eq3(int storage, void* dst, const float* rho, const floa
                             const StoreRef3& ref, float inv_lambda, cudaStream_t st);
 cudaError_t launch_moments3(int storage, const void* src, float* rho, float* u, int64_t n,
                             const StoreRef3& ref, float lambda, cudaStream_t st);
+// The step with the FP64 conserved sums of dst fused in (FP32 with 4-node packs, 16-bit with
+// 8-node packs), written to out[5] as launch_conserved3 does; partials: scratch of
+// step3_sum_scratch(...) doubles (-1 on a CUDA error).
+bool step3_fuses_sums(int storage, int nv, int ny, int nz);
+int64_t step3_sum_scratch(int storage, int nv, const StepArgs3& a);
+cudaError_t launch_step3_conserved(int storage, int um, int nv, const void* src, void* dst,
+                                   const StepArgs3& a, cudaStream_t st, double lambda,
+                                   double* partials, int64_t scratch, double* out);
 // partials: 8 * nblk doubles; out: 5 doubles (sum rho, sum q (3), non-finite nodes).
 cudaError_t launch_conserved3(int storage, const void* src, int64_t n, const StoreRef3& ref,
                               double lambda, double* partials, int nblk, double* out,

@@ -381,11 +381,19 @@ int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]) {
     if (rc != LBMRV_OK) return rc;
     DeviceGuard g(h->device);
     const int nv = choose_width(h, h->f[0], h->f[1]);
-    if (h->dim != 2 || nv < 2) {  // no fused form: the step, then the sums' own pass
+    const bool fused = h->dim == 2 ? nv >= 2
+                                   : step3_fuses_sums(h->storage, nv, (int)h->ny, (int)h->nz);
+    if (!fused) {  // no fused form for this kernel: the step, then the sums' own pass
         rc = lbmrv_step(h, 1);
         return rc != LBMRV_OK ? rc : lbmrv_conserved3(h, out_host);
     }
-    const int64_t need = step_sum_scratch((int)h->nx, (int)h->ny, nv) + 4;
+    if (h->dim == 3 && h->umode == LBMRV_UT_PRESCRIBED && !h->ut0)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_step_conserved: D3Q19 prescribed mode needs a u~0 field");
+    const int64_t scratch = h->dim == 2
+        ? step_sum_scratch((int)h->nx, (int)h->ny, nv)
+        : step3_sum_scratch(h->storage, nv, make_args3(h, h->t + 1));
+    if (scratch < 0) return cuda_fail(h, cudaGetLastError(), "lbmrv_step_conserved");
+    const int64_t need = scratch + 8;  // + the results
     if (need > h->fused_doubles) {
         cudaError_t e = cudaStreamSynchronize(h->stream);  // the old scratch may be in use
         if (e == cudaSuccess) e = cudaFree(h->fused);
@@ -401,23 +409,30 @@ int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]) {
         }
         h->fused_doubles = need;
     }
-    double* res = h->fused + (need - 4);
-    cudaError_t e = launch_step_conserved(
-        h->storage, kernel_mode(h), nv, h->f[h->cur], h->f[1 - h->cur], make_args(h, h->t + 1),
-        h->stream, h->basis, h->rho_ref, h->rho_ref * h->u_ref[0] / h->lambda,
-        h->rho_ref * h->u_ref[1] / h->lambda, h->lambda, h->fused, res);
+    double* res = h->fused + scratch;
+    cudaError_t e;
+    if (h->dim == 2)
+        e = launch_step_conserved(h->storage, kernel_mode(h), nv, h->f[h->cur], h->f[1 - h->cur],
+                                  make_args(h, h->t + 1), h->stream, h->basis, h->rho_ref,
+                                  h->rho_ref * h->u_ref[0] / h->lambda,
+                                  h->rho_ref * h->u_ref[1] / h->lambda, h->lambda, h->fused, res);
+    else
+        e = launch_step3_conserved(h->storage, kernel_mode(h), nv, h->f[h->cur],
+                                   h->f[1 - h->cur], make_args3(h, h->t + 1), h->stream,
+                                   h->lambda, h->fused, scratch, res);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_step_conserved");
     h->cur = 1 - h->cur;
     h->t += 1;
-    double four[4] = {0, 0, 0, 0};
-    e = cudaMemcpyAsync(four, res, sizeof(four), cudaMemcpyDeviceToHost, h->stream);
+    double five[5] = {0, 0, 0, 0, 0};
+    e = cudaMemcpyAsync(five, res, sizeof(double) * (h->dim == 2 ? 4 : 5),
+                        cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_step_conserved");
-    out_host[0] = four[0];
-    out_host[1] = four[1];
-    out_host[2] = four[2];
-    out_host[3] = 0.0;
-    out_host[4] = four[3];
+    if (h->dim == 2) {  // {rho, q_x, q_y, non-finite} -> the lbmrv_conserved3 layout
+        five[4] = five[3];
+        five[3] = 0.0;
+    }
+    for (int k = 0; k < 5; ++k) out_host[k] = five[k];
     if (out_host[4] > 0.0)
         return fail(h, LBMRV_E_NONFINITE,
                     "lbmrv_step_conserved: %.0f nodes hold non-finite values", out_host[4]);

@@ -166,7 +166,7 @@ class D2Q9:
 
     def step_conserved(self, n: int = 1, allow_nonfinite: bool = False):
         """n steps, the last with the sums of conserved3() of its result taken in the same
-        kernel (D2Q9 vector widths; otherwise a separate pass)."""
+        kernel (D2Q9 vector widths, D3Q19 default widths; otherwise a separate pass)."""
         return B.lbmrv_step_conserved(self.h, n, allow_nonfinite=allow_nonfinite)
 
     def state(self) -> torch.Tensor:

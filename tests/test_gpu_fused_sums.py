@@ -97,28 +97,94 @@ def test_fused_sums_full_size_4096_fp32():
         sim.close()
 
 
-@pytest.mark.parametrize("width", [1, 0])
-def test_fallback_paths_match(width):
-    """Scalar kernel (width 1) and D3Q19: the step, then the separate pass."""
+def test_fallback_scalar_kernel_matches():
+    """The scalar kernel (width 1) has no fused form: the step, then the separate pass."""
+    from paper_1312_3297_gb300 import D2Q9
+
+    a, b = _pair(D2Q9, (37, 11), "fluid", "fp32", 1)
+    got = a.step_conserved(4)
+    b.step(4)
+    assert got == b.conserved3()
+
+
+S19 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
+
+
+def _pair3(shape, mode, storage, width, seed=2):
     import torch
 
-    from paper_1312_3297_gb300 import D2Q9, D3Q19
+    from paper_1312_3297_gb300 import D3Q19
 
-    if width == 1:
-        a, b = _pair(D2Q9, (37, 11), "fluid", "fp32", 1)
-        _compare(a, b, 4, 37 * 11)
-        return
-    d = inp.random_flow_3d(16, 12, 8, seed=2)
-    s19 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
+    nx, ny, nz = shape
+    d = inp.random_flow_3d(nx, ny, nz, seed=seed)
+    ut0 = torch.as_tensor(np.random.default_rng(seed + 7).standard_normal((3, nz, ny, nx)),
+                          dtype=torch.float32)
     sims = []
     for _ in range(2):
-        sim = D3Q19(16, 12, 8, s19, mode="fluid", storage="fp16")
+        sim = D3Q19(nx, ny, nz, S19, mode=mode, storage=storage)
+        if mode == "prescribed":
+            sim.set_utilde(ut0, 0.03, 40.0)
+        sim.set_kernel_width(width)
         sim.init_equilibrium(torch.as_tensor(d["rho"], dtype=torch.float32),
                              *(torch.as_tensor(c, dtype=torch.float32) for c in d["u"]))
         sims.append(sim)
-    got = sims[0].step_conserved(4)
-    sims[1].step(4)
-    assert got == sims[1].conserved3()
+    return sims
+
+
+@pytest.mark.parametrize("storage,width,shape", [
+    ("fp32", 4, (16, 12, 8)), ("fp32", 4, (36, 5, 3)),
+    ("fp16", 8, (16, 12, 8)), ("bf16", 8, (16, 12, 8)),
+    ("fp16", 8, (264, 3, 2)), ("bf16", 8, (552, 2, 3))])
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed"])
+def test_fused_sums_d3q19(storage, width, shape, mode):
+    """D3Q19 kernels with the sums fused in (FP32 4-node packs, the staged 16-bit kernel,
+    including rows of several segments): the same state bit for bit and the same sums to
+    FP64 rounding as the step followed by the separate pass."""
+    import torch
+
+    a, b = _pair3(shape, mode, storage, width)
+    n = shape[0] * shape[1] * shape[2]
+    got = a.step_conserved(5)
+    b.step(5)
+    ref = b.conserved3()
+    assert torch.equal(a.state().view(torch.uint8), b.state().view(torch.uint8))
+    np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-12, atol=1e-9 * n)
+    assert got[4] == ref[4] == 0.0
+
+
+@pytest.mark.parametrize("storage,width", [("fp16", 4), ("fp32", 2), ("bf16", 1)])
+def test_fallback_d3q19_matches(storage, width):
+    """D3Q19 widths without a fused form: the step, then the separate pass (exact)."""
+    a, b = _pair3((16, 12, 8), "fluid", storage, width)
+    got = a.step_conserved(4)
+    b.step(4)
+    assert got == b.conserved3()
+
+
+def test_fused_sums_d3q19_full_size_fp16():
+    """The 256^3 FP16 workload the benchmark times (persistent pipeline, one slot per
+    block): fused sums against the separate pass."""
+    import torch
+
+    from paper_1312_3297_gb300 import D3Q19
+
+    L = 256
+    d = inp.taylor_green_3d(L, L, L, u0=0.04)
+    fields = [torch.as_tensor(d["rho"], dtype=torch.float32)] + [
+        torch.as_tensor(c, dtype=torch.float32) for c in d["u"]]
+    del d
+    sims = []
+    for _ in range(2):
+        sim = D3Q19(L, L, L, S19, mode="fluid", storage="fp16")
+        sim.init_equilibrium(*fields)
+        sims.append(sim)
+    got = sims[0].step_conserved(2)
+    sims[1].step(2)
+    ref = sims[1].conserved3()
+    np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-12, atol=1e-9 * L ** 3)
+    assert got[4] == ref[4] == 0.0
+    for sim in sims:
+        sim.close()
 
 
 def test_nonfinite_count_matches_and_is_reported():
