@@ -71,7 +71,7 @@ extern "C" {
 #define LBMRV_E_NOMEM (-3)       /* device allocation failed, or a workspace is too small */
 #define LBMRV_E_NONFINITE (-4)   /* a NaN or infinity was found in the state */
 #define LBMRV_E_TIMEOUT (-5)     /* reserved: no entry point waits on the device */
-#define LBMRV_E_UNSUPPORTED (-6) /* valid request that this build does not implement */
+#define LBMRV_E_UNSUPPORTED (-6) /* valid request that this library does not implement */
 
 /* Lattices. D3Q19 uses 19 velocities (0,0,0); (+-1,0,0), (0,+-1,0), (0,0,+-1);
  * (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0); (1,0,1), (-1,0,-1), (1,0,-1), (-1,0,1);
