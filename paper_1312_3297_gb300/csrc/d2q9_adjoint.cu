@@ -67,6 +67,37 @@ __device__ __forceinline__ void block_accumulate7(float v[7], double* __restrict
 
 constexpr int kAdjThreads = 128;
 
+// The reverse step at one node x (flat index i) of a row whose analytic-field cosine is cy:
+// mu = J_C^T a from the pulled state h and the gathered adjoint ah, into o; the rate and
+// amplitude gradients into acc, the field gradient into aa.dut0.
+template <int UM>
+__device__ __forceinline__ void adjoint_node(const float h[9], const float ah[9], int x,
+                                             float cy, int64_t i, const AdjointArgs& aa,
+                                             float o[9], float acc[7]) {
+    const StepArgs& a = aa.step;
+    float bx, by, ux, uy;
+    base_field<UM>(x, cy, i, a, bx, by);
+    if (UM == UM_FLUID) {
+        const NodeMoments m = node_moments(h);
+        const float ir = recip(a.ref.rho + m.drho);
+        ux = (a.ref.jx + m.jx) * ir;
+        uy = (a.ref.jy + m.jy) * ir;
+    } else {
+        ux = a.amp_t * bx;
+        uy = a.amp_t * by;
+    }
+    float ubx, uby;
+    relax_node_vjp<UM>(h, ah, ux, uy, a.s, a.ref, o, acc, ubx, uby);
+    if (UM == UM_ANALYTIC || UM == UM_FIELD) {
+        acc[6] += aa.da_factor * (ubx * bx + uby * by);
+        if (aa.dut0) {
+            const int64_t n = (int64_t)a.nx * a.ny;
+            aa.dut0[i] += a.amp_t * ubx;
+            aa.dut0[n + i] += a.amp_t * uby;
+        }
+    }
+}
+
 template <int NV, int UM, bool GATHER>
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __restrict__ s_prev,
                                                               const float* __restrict__ a_in,
@@ -101,28 +132,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint_step(const float* __res
                     h[j] = g[j][k];
                     ah[j] = adj[j][k];
                 }
-                const int x = p.x0 + k;
-                const int64_t i = r0 + x;
-                float bx, by, ux, uy;
-                base_field<UM>(x, cy, i, a, bx, by);
-                if (UM == UM_FLUID) {
-                    const NodeMoments m = node_moments(h);
-                    const float ir = recip(a.ref.rho + m.drho);
-                    ux = (a.ref.jx + m.jx) * ir;
-                    uy = (a.ref.jy + m.jy) * ir;
-                } else {
-                    ux = a.amp_t * bx;
-                    uy = a.amp_t * by;
-                }
-                float ubx, uby;
-                relax_node_vjp<UM>(h, ah, ux, uy, a.s, a.ref, o, acc, ubx, uby);
-                if (UM == UM_ANALYTIC || UM == UM_FIELD) {
-                    acc[6] += aa.da_factor * (ubx * bx + uby * by);
-                    if (aa.dut0) {
-                        aa.dut0[i] += a.amp_t * ubx;
-                        aa.dut0[n + i] += a.amp_t * uby;
-                    }
-                }
+                adjoint_node<UM>(h, ah, p.x0 + k, cy, r0 + p.x0 + k, aa, o, acc);
 #pragma unroll
                 for (int j = 0; j < 9; ++j) g[j][k] = o[j];
             }

@@ -6,6 +6,7 @@
 #include <atomic>
 #include <type_traits>
 
+#include "async_copy.cuh"
 #include "d3q19.cuh"
 #include "launch.h"
 #include "pdl.cuh"
@@ -298,21 +299,6 @@ constexpr int kPipeWarps = 4;                                   // per block, 2 
 constexpr int kPipeStages = 2;                                  // segments per warp
 constexpr int kPipeSmem = kPipeWarps * kPipeStages * kPipeStage;  // bytes per block
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait_all_but() {  // all but the latest N groups
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
 
 // x shift of plane j: 0 none, 1 from the left (x - 1), 2 from the right (x + 1); relation
 // (transport) in pull form. hslot: the plane's halo slot (x-moving planes only).
