@@ -205,3 +205,19 @@ def test_nonfinite_count_matches_and_is_reported():
         a.step_conserved(1)
     with pytest.raises(binding.LbmrvError):
         b.step_conserved(0)
+
+
+def test_scratch_grows_when_the_width_changes():
+    """A call at 4-node packs, then at 2-node packs (twice the step blocks): the scratch is
+    reallocated and the sums stay equal to the separate pass."""
+    from paper_1312_3297_gb300 import D2Q9
+
+    shape = (512, 64)
+    a, b = _pair(D2Q9, shape, "fluid", "fp32", 4)
+    _compare(a, b, 3, shape[0] * shape[1])
+    for sim in (a, b):
+        sim.set_kernel_width(2)
+    got = a.step_conserved(2)
+    b.step(2)
+    ref = b.conserved3()
+    np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-12, atol=1e-9 * shape[0] * shape[1])
