@@ -218,11 +218,12 @@ def _window_oracle(fields_full, center, R, steps, s, mode, amp, period, nxg, nyg
     return S[:, R, R]
 
 
-@pytest.mark.parametrize("mode", ["prescribed", "zero", "fluid"])
+@pytest.mark.parametrize("mode", ["prescribed", "zero", "fluid", "prescribed_stored"])
 def test_full_size_4096_sampled_parity(mode):
-    """Taylor-Green vortex u0 = 0.04 on 4096^2 in the benchmark's launch configuration:
+    """Taylor-Green vortex u0 = 0.04 on 4096^2 in the benchmark's launch configurations:
     sampled nodes (corners, wrap edges, vector-pack and warp boundaries, interior) against
-    the oracle on their dependency cone."""
+    the oracle on their dependency cone. prescribed_stored: the same u~(x, t), its base
+    field (cos 2 pi y/L, sin 2 pi x/L) read from a device array instead of computed."""
     import torch
 
     from paper_1312_3297_gb300 import D2Q9
@@ -231,9 +232,14 @@ def test_full_size_4096_sampled_parity(mode):
     s = [0, 0, 0, 1.4, 1.8, 1.8, 1.2, 1.2, 1.4]
     d = inp.taylor_green(L, L, u0=0.04)
     fields = f32_fields(d)
-    sim = D2Q9(L, L, s, mode=mode)
+    sim = D2Q9(L, L, s, mode="prescribed" if mode == "prescribed_stored" else mode)
     if mode == "prescribed":
         sim.set_utilde(None, 0.03, 1000.0)
+    elif mode == "prescribed_stored":
+        k = 2 * np.pi * np.arange(L) / L
+        base = np.stack([np.repeat(np.cos(k)[:, None], L, axis=1),
+                         np.repeat(np.sin(k)[None, :], L, axis=0)]).astype(np.float32)
+        sim.set_utilde(torch.as_tensor(base), 0.03, 1000.0)
     sim.init_equilibrium(*(torch.as_tensor(a) for a in fields))
     sim.step(steps)
     g = sim.state()
@@ -241,7 +247,7 @@ def test_full_size_4096_sampled_parity(mode):
     centers = [(0, 0), (L - 1, L - 1), (0, L - 1), (L - 1, 0), (3, 5), (4, 5), (127, 9),
                (128, 9), (511, 2000), (512, 2001), (L - 4, 17), (L - 5, 17)]
     centers += [tuple(int(v) for v in rng.integers(0, L, 2)) for _ in range(6)]
-    mid = {"zero": 0, "fluid": 1, "prescribed": 2}[mode]
+    mid = {"zero": 0, "fluid": 1, "prescribed": 2, "prescribed_stored": 2}[mode]
     fmax = 0.0
     errs = []
     for c in centers:
