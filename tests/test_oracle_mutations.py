@@ -33,6 +33,12 @@ CASES = [
      "test_basis_is_unisolvent_and_shift_closed", {"lam": 1.0}),
     (9, "D3Q19 transport pulling from z + v_z", "test_oracle3d_pins",
      "test_transport_moves_populations_along_velocities", {}),
+    (1, "the (v.u)^2 term of the equilibrium dropped (brute force)", "test_oracle_bruteforce",
+     "test_definition_oracle_equals_brute_force",
+     {"orc": True, "nx": 3, "ny": 3, "mode": 1, "lam": 1.0}),
+    (2, "transport pulling from x + v_j (brute force)", "test_oracle_bruteforce",
+     "test_definition_oracle_equals_brute_force",
+     {"orc": True, "nx": 4, "ny": 5, "mode": 0, "lam": 2.0}),
 ]
 
 
@@ -58,7 +64,8 @@ def _run_pin(module, name, kw):
     return fn(**args)
 
 
-@pytest.mark.parametrize("k,what,module,name,kw", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("k,what,module,name,kw", CASES,
+                         ids=[f"{c[0]}-{c[3]}" for c in CASES])
 def test_pin_catches_planted_mistake(oracle_variant, k, what, module, name, kw):
     oracle_variant(k)
     with pytest.raises(AssertionError):
