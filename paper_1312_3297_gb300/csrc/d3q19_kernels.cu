@@ -291,9 +291,11 @@ __global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict_
 // blocks per SM with up to 255 registers per thread (measured on
 // GB300: more warps with fewer registers spill, and deeper rings with fewer warps issue
 // too slowly).
-constexpr int kPipeSeg = 32 * 8;                               // nodes per row segment
-constexpr int kPipeData = 19 * 32 * 16;                        // packs of one stage
+constexpr int kPipeNpl = 8;  // nodes per lane (4: 168 registers, 3 blocks per SM, slower)
+constexpr int kPipeSeg = 32 * kPipeNpl;                         // nodes per row segment
+constexpr int kPipeData = 19 * 32 * 2 * kPipeNpl;               // packs of one stage
 constexpr int kPipeStage = kPipeData + 10 * 32 * 4;            // + halo words
+constexpr int kPipeBlocksPerSm = kPipeNpl == 8 ? 2 : 3;
 
 constexpr int kPipeWarps = 4;                                   // per block, 2 blocks per SM
 constexpr int kPipeStages = 2;                                  // segments per warp
@@ -350,11 +352,12 @@ constexpr int pipe_plane_groups() {
 }
 
 template <typename T, int UM, int RCP, bool SUMS = false>
-__global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __restrict__ src,
+__global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pipe(const T* __restrict__ src,
                                                                    T* __restrict__ dst,
                                                                    StepArgs3 a,
                                                                    double* __restrict__ part) {
     constexpr int S = kPipeStages;
+    constexpr int NPL = kPipeNpl, P = NPL / 2;  // nodes and node pairs per lane
     double sums[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // SUMS: the stored result's moments
     pdl_wait_prior();
     pdl_allow_next();
@@ -394,23 +397,26 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
     // queue the copies of planes [LO, HI) of the item at `c` into buffer `stage`
     auto copy = [&](const Cursor& c, int stage, auto lo, auto hi) {
         constexpr int LO = decltype(lo)::value, HI = decltype(hi)::value;
-        const int x0 = c.seg * kPipeSeg + lane * 8;
+        const int x0 = c.seg * kPipeSeg + lane * NPL;
         if (c.z < nz && x0 < nx) {
             const RowNums3 r(c.y, c.z, ny, nz);
             unsigned char* sb = wbuf + stage * kPipeStage;
-            const int xl = (x0 == 0 ? nx : x0) - 2;   // word (x0-2, x0-1), periodic
-            const int xr = x0 + 8 >= nx ? 0 : x0 + 8;  // word (x0+8, x0+9), periodic
+            const int xl = (x0 == 0 ? nx : x0) - 2;       // word (x0-2, x0-1), periodic
+            const int xr = x0 + NPL >= nx ? 0 : x0 + NPL;  // word after the pack, periodic
 #pragma unroll
             for (int j = LO; j < HI; ++j) {
                 const T* row = src + j * n + (int64_t)plane_rownum(r, j) * nx;
-                cp_async16(sb + (j * 32 + lane) * 16, row + x0);
+                if constexpr (NPL == 8)
+                    cp_async16(sb + (j * 32 + lane) * 16, row + x0);
+                else
+                    cp_async8(sb + (j * 32 + lane) * 8, row + x0);
                 if (plane_hslot(j) >= 0)
                     cp_async4(sb + kPipeData + (plane_hslot(j) * 32 + lane) * 4,
                               row + (plane_shift(j) == 1 ? xl : xr));
             }
         }
     };
-    constexpr int Q = S == 2 ? pipe_plane_groups<T, UM>() : 1;
+    constexpr int Q = S != 2 ? 1 : pipe_plane_groups<T, UM>() < P ? pipe_plane_groups<T, UM>() : P;
     using I0 = std::integral_constant<int, 0>;
     using I19 = std::integral_constant<int, 19>;
     auto copy_group = [&](const Cursor& c, int stage, auto q) {
@@ -436,7 +442,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
             if (k == 2) copy_group(ahead, fill, std::integral_constant<int, 2>());
             if (k == 3) copy_group(ahead, fill, std::integral_constant<int, 3>());
         } else if constexpr (Q == 2) {
-            if (k == 2) copy_group(ahead, fill, std::integral_constant<int, 1>());
+            if (k == P / 2) copy_group(ahead, fill, std::integral_constant<int, 1>());
         }
     };
     while (cur.z < nz) {
@@ -449,29 +455,41 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
             cp_async_wait_all_but<S - 1>();  // the oldest group: the item at `cur`
         }
         __syncwarp();
-        const int y = cur.y, z = cur.z, x0 = cur.seg * kPipeSeg + lane * 8;
+        const int y = cur.y, z = cur.z, x0 = cur.seg * kPipeSeg + lane * NPL;
         if (x0 < nx) {
             const unsigned char* sb = wbuf + stage * kPipeStage;
             const int64_t r00 = (int64_t)(z * ny + y) * nx;
             // pair k of an x-moving plane straddles words k and k + 1 of (left halo, pack)
             // or (pack, right halo)
-            uint32_t w[19][4];
+            uint32_t w[19][P];
 #pragma unroll
             for (int j = 0; j < 19; ++j) {
-                const uint4 v = *reinterpret_cast<const uint4*>(sb + (j * 32 + lane) * 16);
+                uint32_t e[P + 2];
                 const uint32_t hw = plane_hslot(j) >= 0
                     ? *reinterpret_cast<const uint32_t*>(sb + kPipeData +
                                                          (plane_hslot(j) * 32 + lane) * 4)
                     : 0u;
-                const uint32_t e[6] = {hw, v.x, v.y, v.z, v.w, hw};
+                e[0] = hw;
+                e[P + 1] = hw;
+                if constexpr (NPL == 8) {
+                    const uint4 v = *reinterpret_cast<const uint4*>(sb + (j * 32 + lane) * 16);
+                    e[1] = v.x;
+                    e[2] = v.y;
+                    e[3] = v.z;
+                    e[4] = v.w;
+                } else {
+                    const uint2 v = *reinterpret_cast<const uint2*>(sb + (j * 32 + lane) * 8);
+                    e[1] = v.x;
+                    e[2] = v.y;
+                }
 #pragma unroll
-                for (int k = 0; k < 4; ++k)
+                for (int k = 0; k < P; ++k)
                     w[j][k] = plane_shift(j) == 1 ? __byte_perm(e[k], e[k + 1], 0x5432)
                             : plane_shift(j) == 2 ? __byte_perm(e[k + 1], e[k + 2], 0x5432)
                                                   : e[k + 1];
             }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
+            for (int k = 0; k < P; ++k) {
                 if constexpr (Q > 1) issue_groups_before(k);
                 const int64_t i = r00 + x0 + 2 * k;  // first node of the pair
                 F2 h[19];
@@ -494,12 +512,12 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
                 for (int j = 0; j < 19; ++j) w[j][k] = add_to_pair<T>(w[j][k], h[j]);
             }
 #pragma unroll
-            for (int j = 0; j < 19; ++j) store_raw16<8>(dst + j * n + r00 + x0, w[j]);
+            for (int j = 0; j < 19; ++j) store_raw16<NPL>(dst + j * n + r00 + x0, w[j]);
             if constexpr (SUMS) {
-                float rs[4] = {0.f, 0.f, 0.f, 0.f};  // 8 nodes in FP32, then FP64
+                float rs[4] = {0.f, 0.f, 0.f, 0.f};  // NPL nodes in FP32, then FP64
                 int bad = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
+                for (int k = 0; k < P; ++k) {
                     float lo[19], hi[19];
 #pragma unroll
                     for (int j = 0; j < 19; ++j) {
@@ -516,7 +534,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, 2) k_step3_pipe(const T* __re
             }
         } else if constexpr (Q > 1) {
 #pragma unroll
-            for (int k = 1; k < 4; ++k) issue_groups_before(k);  // as the relaxation would
+            for (int k = 1; k < P; ++k) issue_groups_before(k);  // as the relaxation would
         }
         if constexpr (Q > 1) cp_async_commit();
         __syncwarp();  // every lane is done with `stage` before it is refilled
@@ -712,7 +730,7 @@ cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStr
         if (e != cudaSuccess) return e;
         // persistent: no more blocks than are resident at once (work is split between
         // warps up front)
-        per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+        per_sm = per_sm < 1 ? 1 : (per_sm > kPipeBlocksPerSm ? kPipeBlocksPerSm : per_sm);
         full = per_sm * sms;
         if (dev < kMaxDevices) resident[dev].store(full, std::memory_order_relaxed);
     }
@@ -810,7 +828,7 @@ int64_t step3_sum_scratch(int storage, int nv, const StepArgs3& a) {
         if (cudaGetDevice(&dev) != cudaSuccess ||
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             return -1;
-        slots = 2LL * sms;  // the pipeline's persistent grid: at most 2 blocks per SM
+        slots = (int64_t)kPipeBlocksPerSm * sms;  // the pipeline's persistent grid
     }
     return 8 * slots + 8 * ((slots + kReduceThreads - 1) / kReduceThreads);
 }
