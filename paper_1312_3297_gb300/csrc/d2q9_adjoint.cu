@@ -292,11 +292,6 @@ __global__ void k_partials_final(const double* __restrict__ part, int nblk,
     }
 }
 
-int grid1d(int64_t n, int threads) {
-    int64_t b = (n + threads - 1) / threads;
-    const int64_t cap = 152LL * 16;
-    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
 
 }  // namespace
 
@@ -369,13 +364,13 @@ cudaError_t launch_acc_final(const double* acc, int64_t nblk, double* out, cudaS
 
 cudaError_t launch_equilibrium_vjp(const float* rho, const float* u, const float* a, float* drho,
                                    float* du, int64_t n, float inv_lambda, cudaStream_t st) {
-    k_equilibrium_vjp<<<grid1d(n, 256), 256, 0, st>>>(rho, u, a, drho, du, n, inv_lambda);
+    k_equilibrium_vjp<<<grid_stride_blocks(n, 256), 256, 0, st>>>(rho, u, a, drho, du, n, inv_lambda);
     return cudaGetLastError();
 }
 
 cudaError_t launch_moments_vjp(const float* g, const float* drho, const float* du, float* out,
                                int64_t n, const StoreRef& ref, float lambda, cudaStream_t st) {
-    k_moments_vjp<<<grid1d(n, 256), 256, 0, st>>>(g, drho, du, out, n, ref, lambda);
+    k_moments_vjp<<<grid_stride_blocks(n, 256), 256, 0, st>>>(g, drho, du, out, n, ref, lambda);
     return cudaGetLastError();
 }
 

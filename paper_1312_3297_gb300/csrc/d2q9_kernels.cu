@@ -2,6 +2,8 @@
 // initialisation, moments and FP64 conserved-quantity reductions.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "d2q9.cuh"
 #include "launch.h"
 #include "pdl.cuh"
@@ -352,11 +354,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_sum_partials(const double* _
     block_sum4<kReduceThreads>(v, out + 4 * (int64_t)blockIdx.x);
 }
 
-int grid_for(int64_t n, int threads) {
-    int64_t b = (n + threads - 1) / threads;
-    const int64_t cap = 152LL * 16;
-    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
 
 template <typename T, int NV, int UM, int BASIS>
 cudaError_t launch_vec(const T* s, T* d, const StepArgs& a, cudaStream_t st, double* part) {
@@ -416,6 +413,21 @@ cudaError_t step_dispatch_basis(const void* src, void* dst, const StepArgs& a, c
 }
 
 }  // namespace
+
+int grid_stride_blocks(int64_t n, int threads) {
+    constexpr int kMaxDevices = 64;
+    static std::atomic<int> sms_of[kMaxDevices];
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        sms = dev < kMaxDevices ? sms_of[dev].load(std::memory_order_relaxed) : 0;
+        if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                            cudaSuccess && dev < kMaxDevices)
+            sms_of[dev].store(sms, std::memory_order_relaxed);
+    }
+    if (sms <= 0) sms = 152;  // no answer from the runtime: the GB300's count
+    const int64_t b = (n + threads - 1) / threads, cap = 16LL * sms;
+    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
+}
 
 int step_vector_width(int storage, int nx) {
     // Widest pack that divides nx, up to the width measured fastest on GB300 (8192^2 sweep):
@@ -480,7 +492,7 @@ cudaError_t launch_step_conserved(int storage, int um, int nv, const void* src, 
 cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float* u, int64_t n,
                            const StoreRef& rho_ref, float inv_lambda, cudaStream_t st,
                            int basis) {
-    const int g = grid_for(n, 256);
+    const int g = grid_stride_blocks(n, 256);
     if (basis == 1) {
         switch (storage) {
             case kStoreF32:
@@ -519,7 +531,7 @@ cudaError_t launch_init_eq(int storage, void* dst, const float* rho, const float
 
 cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, int64_t n,
                            const StoreRef& rho_ref, float lambda, cudaStream_t st) {
-    const int g = grid_for(n, 256);
+    const int g = grid_stride_blocks(n, 256);
     switch (storage) {
         case kStoreF32:
             k_moments<float><<<g, 256, 0, st>>>(static_cast<const float*>(src), rho, u, n,

@@ -667,11 +667,6 @@ __global__ void k_conserved3_final(const double* __restrict__ part, int nblk, do
     }
 }
 
-int grid1d3(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    const int64_t cap = 152LL * 16;
-    return (int)(b < 1 ? 1 : (b > cap ? cap : b));
-}
 
 // Block shape for NV-node packs on rows of nx nodes: 32 to kThreads3 threads along x (a
 // multiple of 32), and, for kernels that take it, the rest of the block on further rows.
@@ -882,7 +877,7 @@ cudaError_t launch_step3(int storage, int um, int nv, const void* src, void* dst
 
 cudaError_t launch_init_eq3(int storage, void* dst, const float* rho, const float* u, int64_t n,
                             const StoreRef3& ref, float inv_lambda, cudaStream_t st) {
-    const int g = grid1d3(n);
+    const int g = grid_stride_blocks(n, 256);
     switch (storage) {
         case kStoreF32:
             k_init_eq3<float><<<g, 256, 0, st>>>(static_cast<float*>(dst), rho, u, n, ref, inv_lambda);
@@ -901,7 +896,7 @@ cudaError_t launch_init_eq3(int storage, void* dst, const float* rho, const floa
 
 cudaError_t launch_moments3(int storage, const void* src, float* rho, float* u, int64_t n,
                             const StoreRef3& ref, float lambda, cudaStream_t st) {
-    const int g = grid1d3(n);
+    const int g = grid_stride_blocks(n, 256);
     switch (storage) {
         case kStoreF32:
             k_moments3<float><<<g, 256, 0, st>>>(static_cast<const float*>(src), rho, u, n, ref, lambda);

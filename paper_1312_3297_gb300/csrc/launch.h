@@ -12,7 +12,14 @@ namespace lbmrv {
 enum { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
 
 constexpr int kReduceThreads = 256;
+// Most partial sums of a reduction (8 blocks per SM of a 152-SM GB300; any GPU works with
+// it). A compile-time constant because it sizes the fixed scratch of
+// lbmrv_conserved_noalloc.
 constexpr int kReduceMaxBlocks = 152 * 8;
+
+// Blocks of a grid-stride kernel over n items with `threads` per block: enough for every
+// item, at most 16 per SM of the current device (found once per device).
+int grid_stride_blocks(int64_t n, int threads);
 
 // Widest vector pack (nodes per thread) the fused step can use for this row length.
 int step_vector_width(int storage, int nx);
