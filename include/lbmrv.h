@@ -154,8 +154,10 @@ LBMRV_API int lbmrv_set_stream(lbmrv_t h, void* stream);
  * node per thread (any lattice), 2/4/8 force that many consecutive nodes per thread with
  * vector loads (must divide nx; at most 4 for FP32, 8 for 16-bit storage; the state
  * buffers must be aligned to the pack). All variants compute the same scheme to rounding;
- * this exists for testing and tuning. It also sets the width (1, 2 or 4) of the adjoint
- * kernel. */
+ * this exists for testing and tuning. Automatic widths: D2Q9 4 (FP32) or 8 (16-bit);
+ * D3Q19 4 (FP32) or 8 (16-bit: a kernel that stages 256-node row segments in shared
+ * memory, bit-identical to 4-node packs). It also sets the width (1, 2 or 4) of the
+ * adjoint kernel. */
 LBMRV_API int lbmrv_set_kernel_width(lbmrv_t h, int nodes_per_thread);
 
 /* Prescribed relative velocity u~(x, t) = amplitude * u~0(x) * cos(2 pi t / period),
