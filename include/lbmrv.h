@@ -260,15 +260,17 @@ LBMRV_API int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void
                                          size_t ws_bytes);
 
 /* Reverse sweep of the last lbmrv_forward_checkpointed(n, seg, ws_dev) (same arguments).
- *   dL_dS_dev     device FP32 [9][nx*ny]: dL/dS_N, gradient of the loss with respect to
- *                 the stored state after the n steps (e.g. from lbmrv_kinetic_energy or
- *                 lbmrv_moments_vjp). Not modified.
- *   dL_dS0_dev    device FP32 [9][nx*ny] out: dL/dS_0 (may alias nothing else).
+ *   dL_dS_dev     device FP32 [9][nx*ny], 16-byte aligned: dL/dS_N, gradient of the loss
+ *                 with respect to the stored state after the n steps (e.g. from
+ *                 lbmrv_kinetic_energy or lbmrv_moments_vjp). Not modified.
+ *   dL_dS0_dev    device FP32 [9][nx*ny] out, 16-byte aligned: dL/dS_0 (may alias nothing
+ *                 else).
  *   dL_ds_host    9 doubles out, or NULL: dL/ds_k (0 for the conserved k < 3).
  *   dL_damp_host  1 double out, or NULL: dL/dA for the prescribed mode (0 otherwise).
  *   dL_dut0_dev   device FP32 [2][nx*ny] out, or NULL: dL/du~0(x) for the prescribed mode
  *                 with a caller field or the analytic one (overwritten).
- * Synchronous (returns host values). The handle's current state is not changed. */
+ * Synchronous (returns host values). The handle's current state is not changed.
+ * LBMRV_E_INVAL for NULL or unaligned gradient buffers, before any work is queued. */
 LBMRV_API int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_bytes,
                             const float* dL_dS_dev, float* dL_dS0_dev, double* dL_ds_host,
                             double* dL_damp_host, float* dL_dut0_dev);

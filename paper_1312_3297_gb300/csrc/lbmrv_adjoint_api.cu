@@ -123,6 +123,10 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
     if (rc != LBMRV_OK) return rc;
     if (!dL_dS_dev || !dL_dS0_dev)
         return fail(h, LBMRV_E_INVAL, "lbmrv_adjoint: dL/dS_N and dL/dS_0 buffers are required");
+    // the reverse step reads dL/dS_N, and the final gather writes dL/dS_0, in 16-byte packs
+    if (reinterpret_cast<uintptr_t>(dL_dS_dev) % 16 || reinterpret_cast<uintptr_t>(dL_dS0_dev) % 16)
+        return fail(h, LBMRV_E_INVAL,
+                    "lbmrv_adjoint: dL/dS_N and dL/dS_0 must be 16-byte aligned device buffers");
     if (!h->ckpt_valid || h->ckpt_n != n || h->ckpt_seg != seg || h->ckpt_ws != ws_dev)
         return fail(h, LBMRV_E_INVAL,
                     "lbmrv_adjoint: no matching lbmrv_forward_checkpointed(n, seg, ws) before");

@@ -206,6 +206,8 @@ class D2Q9:
         dut = (torch.empty((2, self.ny, self.nx), dtype=torch.float32, device=self.device)
                if field_grad else None)
         dL_dS = dL_dS.contiguous()
+        if dL_dS.data_ptr() % 16:  # the library reads it in 16-byte packs
+            dL_dS = dL_dS.clone()
         self._sync_in()
         ds, da = B.lbmrv_adjoint(self.h, n, seg, ws, ws.numel(), dL_dS, d0, dut)
         self._sync_out()

@@ -224,3 +224,35 @@ def test_velocity_probe_misfit_through_autograd(mode):
     assert abs(s_nu.grad.item() - gs.item()) <= TOL * abs(gs.item())
     if mode == "prescribed":
         assert abs(amp.grad.item() - ga.item()) <= TOL * abs(ga.item())
+
+
+def test_unaligned_gradient_buffers():
+    """The C entry point rejects dL/dS buffers that are not 16-byte aligned before queuing
+    any work; the Python wrapper copies a misaligned dL/dS view into aligned storage and
+    gives the gradient of the aligned call."""
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9, binding as B
+
+    nx, ny, steps = 64, 32, 12
+    d = inp.noisy_shear_wave(nx, ny, seed=6)
+    sim = D2Q9(nx, ny, S, mode="fluid")
+    sim.init_equilibrium(*(torch.as_tensor(d[k], dtype=torch.float32) for k in ("rho", "ux", "uy")))
+    ws = sim.adjoint_workspace(steps, 4)
+    sim.forward_checkpointed(steps, 4, ws)
+    _, dlds = sim.kinetic_energy(grad=True)
+    n9 = 9 * nx * ny
+    big = torch.zeros(n9 + 4, dtype=torch.float32, device="cuda")
+    big[1:1 + n9] = dlds.reshape(-1)
+    view = big[1:1 + n9].view(9, ny, nx)  # contiguous, 4 bytes past a 16-byte boundary
+    out = torch.empty_like(dlds)
+    with pytest.raises(B.LbmrvError) as ei:
+        B.lbmrv_adjoint(sim.h, steps, 4, ws, ws.numel(), view.data_ptr(), out)
+    assert ei.value.status == B.LBMRV_E_INVAL and "aligned" in str(ei.value)
+    with pytest.raises(B.LbmrvError):
+        B.lbmrv_adjoint(sim.h, steps, 4, ws, ws.numel(), dlds, big[1:1 + n9].data_ptr())
+    d_ok = sim.adjoint(steps, 4, ws, dlds)
+    d_view = sim.adjoint(steps, 4, ws, view)
+    np.testing.assert_array_equal(d_view[0].cpu().numpy(), d_ok[0].cpu().numpy())
+    assert d_view[1] == d_ok[1]
+    sim.close()
