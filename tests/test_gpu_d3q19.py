@@ -153,3 +153,45 @@ def test_full_size_256_sampled_parity_and_conservation(storage, tol, mass_tol, m
     for a in (1, 2, 3):
         assert abs(c1[a] - c0[a]) < mom_tol * c0[0] * 0.04
     sim.close()
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", TOL), ("fp16", 2e-4)])
+def test_512_cubed_plane_offsets_past_31_bits(storage, tol):
+    """512^3 (134 M nodes): the offsets j * n of the upper planes pass 2^31 elements, so any
+    32-bit plane arithmetic would read the wrong place. Sampled nodes (plane-crossing
+    corners, pack and segment edges, random places) against the oracle on their dependency
+    cone, in the default kernels (FP32 4-node packs; FP16 the staged 8-node packs)."""
+    import torch
+
+    from oracle import d3q19 as o3
+    from paper_1312_3297_gb300 import D3Q19
+
+    L, steps = 512, 3
+    d = inp.taylor_green_3d(L, L, L, u0=0.04)
+    rho, u = inp.to_f32_exact(d["rho"]), inp.to_f32_exact(d["u"])
+    del d
+    sim = D3Q19(L, L, L, S3, mode="fluid", storage=storage)
+    sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in u))
+    sim.step(steps)
+    g = sim.state()
+    fref = reference_populations3(sim.rho_ref, (0, 0, 0))
+    rng = np.random.default_rng(5)
+    centers = [(0, 0, 0), (L - 1, L - 1, L - 1), (255, 256, 511), (256, 511, 0),
+               (7, 1, 300), (8, 2, 301), (L - 8, 400, 1)]
+    centers += [tuple(int(v) for v in rng.integers(0, L, 3)) for _ in range(3)]
+    R = steps + 1
+    errs, fmax = [], 0.0
+    for cx, cy, cz in centers:
+        xs = (cx + np.arange(-R, R + 1)) % L
+        ys = (cy + np.arange(-R, R + 1)) % L
+        zs = (cz + np.arange(-R, R + 1)) % L
+        sub_rho = rho[np.ix_(zs, ys, xs)]
+        sub_u = u[:, zs][:, :, ys][:, :, :, xs]
+        f0 = o3.init_equilibrium(sub_rho, sub_u, 1.0)
+        S = o3.post_collision_state(f0, 1.0, np.array(S3, float), 1, steps, nthreads=8)
+        ref = S[:, R, R, R]
+        got = g[:, cz, cy, cx].double().cpu().numpy() + fref
+        errs.append(np.abs(got - ref).max())
+        fmax = max(fmax, np.abs(ref).max())
+    assert max(errs) / fmax <= tol, errs
+    sim.close()
