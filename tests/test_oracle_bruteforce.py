@@ -106,3 +106,70 @@ def test_prescribed_caller_field_equals_brute_force(orc):
     ref = _brute_run(f0, lam, S_PAPER, 2, 3, ut0=ut0, **kw)
     got = orc.run(f0, lam, S_PAPER, 2, 3, ut0=ut0, **kw)
     np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)
+
+
+# ---------------------------------------------------------------- Geier's basis
+GEIER = [lambda X, Y: 1.0, lambda X, Y: X, lambda X, Y: Y, lambda X, Y: X * X + Y * Y,
+         lambda X, Y: X * X - Y * Y, lambda X, Y: X * Y, lambda X, Y: X * Y * Y,
+         lambda X, Y: X * X * Y, lambda X, Y: X * X * Y * Y]
+S_GEIER = np.array([0, 0, 0, 1.3, 1.8, 1.8, 1.5, 1.5, 1.2])
+
+
+def _geier_matrix(ut, lam):
+    return np.array([[GEIER[k](lam * CXY[j, 0] - ut[0], lam * CXY[j, 1] - ut[1])
+                      for j in range(9)] for k in range(9)])
+
+
+def _maxwellian_populations(rho, u, lam):
+    """The populations whose Geier moments about u are those of the Maxwellian with
+    c^2 = lambda^2 / 3: (rho, 0, 0, 2 rho c^2, 0, 0, 0, 0, rho c^4) (the reading of
+    Section 1.3 on Geier's equilibria), solved for directly."""
+    c2 = lam * lam / 3
+    return np.linalg.solve(_geier_matrix(u, lam),
+                           np.array([rho, 0, 0, 2 * rho * c2, 0, 0, 0, 0, rho * c2 * c2]))
+
+
+def _brute_run_geier(f, lam, s, mode, steps, amp=0.0, period=1.0):
+    f = f.copy()
+    _, ny, nx = f.shape
+    for t in range(steps):
+        post = np.empty_like(f)
+        for y in range(ny):
+            for x in range(nx):
+                g = f[:, y, x]
+                rho = g.sum()
+                q = lam * (CXY.T @ g)
+                if mode == 0:
+                    ut = np.zeros(2)
+                elif mode == 1:
+                    ut = q / rho
+                else:
+                    ut = amp * np.array([np.cos(2 * np.pi * y / ny), np.sin(2 * np.pi * x / nx)]
+                                        ) * np.cos(2 * np.pi * t / period)
+                M = _geier_matrix(ut, lam)
+                m = M @ g
+                meq = M @ _maxwellian_populations(rho, q / rho, lam)
+                post[:, y, x] = np.linalg.solve(M, m + s * (meq - m))
+        for j in range(9):
+            f[j] = np.roll(post[j], shift=(CXY[j, 1], CXY[j, 0]), axis=(0, 1))
+    return f
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("lam", [1.0, 2.0])
+def test_geier_definition_oracle_equals_brute_force(orc, mode, lam):
+    """The oracle's definition in Geier's basis (product-form equilibrium) against the
+    numpy statement above, whose equilibrium is solved from the Maxwellian moments."""
+    rng = np.random.default_rng(300 + 10 * mode + int(lam))
+    nx, ny = 4, 3
+    rho = 1 + 0.05 * rng.standard_normal((ny, nx))
+    u = lam * 0.06 * rng.standard_normal((2, ny, nx))
+    f0 = np.empty((9, ny, nx))
+    for y in range(ny):
+        for x in range(nx):
+            f0[:, y, x] = _maxwellian_populations(rho[y, x], u[:, y, x], lam)
+    f0 *= 1 + 0.05 * rng.standard_normal(f0.shape)
+    kw = dict(amp=0.05 * lam, period=7.0) if mode == 2 else {}
+    ref = _brute_run_geier(f0, lam, S_GEIER, mode, 3, **kw)
+    got = orc.run(f0, lam, S_GEIER, mode, 3, method=orc.METHOD_GEIER, **kw)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=1e-13)

@@ -39,6 +39,8 @@ CASES = [
     (2, "transport pulling from x + v_j (brute force)", "test_oracle_bruteforce",
      "test_definition_oracle_equals_brute_force",
      {"orc": True, "nx": 4, "ny": 5, "mode": 0, "lam": 2.0}),
+    (5, "rates applied to the wrong moments (Geier brute force)", "test_oracle_bruteforce",
+     "test_geier_definition_oracle_equals_brute_force", {"orc": True, "mode": 1, "lam": 1.0}),
     (7, "D3Q19 edge weight 1/18 (brute force)", "test_oracle3d_bruteforce",
      "test_d3q19_oracle_equals_brute_force", {"shape": (3, 3, 3), "mode": 1, "lam": 1.0}),
     (8, "D3Q19 basis polynomial ZY^2 written as YZ^2 (brute force)", "test_oracle3d_bruteforce",
