@@ -297,6 +297,16 @@ def gpu_arm(args):
     sim.close()
     per_step_ms = ms / args.steps
     mlups = job_mlups(n, world, args.steps, ms)
+    e2e = None
+    if not args.no_e2e and size == L and args.storage == "fp32" and args.mode == "prescribed" \
+            and args.lattice == "d2q9":
+        # every rank runs its replica end to end; the job's figure takes the slowest rank
+        if world > 1:
+            dist.barrier()
+        e2e = e2e_measure(torch, D2Q9, inp, fields, args.steps)
+        worst = max_over_ranks(e2e.pop("seconds"), torch.device("cuda", local))
+        e2e["value"] = round(job_mlups(n, world, args.steps, worst * 1e3), 1)
+        e2e["runs_rank0"] = e2e.pop("runs")
     bpn = BYTES_PER_NODE[args.storage] * (19 / 9 if args.lattice == "d3q19" else 1)
     achieved = bpn * n / (per_step_ms * 1e-3) / 1e9
     headline = (size == L and args.storage == "fp32" and args.mode == "prescribed"
@@ -331,8 +341,6 @@ def gpu_arm(args):
             extras["conserved_sums_4096"] = sums_measure(torch, D2Q9, inp, fields)
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
             extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
-        e2e = (e2e_measure(torch, D2Q9, inp, fields, args.steps)
-               if not args.no_e2e and headline else None)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
         out = {
             "metric": METRIC, "value": round(mlups, 1), "unit": "MLUPS", "n_gpus": world,
@@ -353,7 +361,7 @@ def gpu_arm(args):
                          "kernel": kernel_label(args.lattice, args.storage, size, args.mode)},
             "clocks": clock_info,
             "e2e": e2e,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * world,  # one step kernel per step and replica
             "cpu_baseline": cpu,
             "modes": extras,
             "wall_ms_timed_region": round(wall_ms, 2),
@@ -554,12 +562,14 @@ def e2e_measure(torch, D2Q9, inp, fields, steps):
         sim.moments_host(rho_o, u_o)  # synchronous
         runs.append(n * steps / (time.perf_counter() - t0) / 1e6)
     sim.close()
-    return {"value": round(statistics.median(runs), 1), "unit": "MLUPS",
+    med = statistics.median(runs)
+    return {"value": round(med, 1), "unit": "MLUPS",
             "h2d_bytes_per_step": round(12 * n / steps, 1),
             "d2h_bytes_per_step": round(12 * n / steps, 1),
             "unit_of_work": f"one {steps}-step run from host rho,u to host rho,u "
                             "(median of 3 runs)",
-            "runs": [round(r, 1) for r in runs]}
+            "runs": [round(r, 1) for r in runs],
+            "seconds": n * steps / (med * 1e6)}
 
 
 # ------------------------------------------------------------------ CPU oracle
