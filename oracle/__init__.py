@@ -51,14 +51,15 @@ _lib = None
 _openmp = False
 
 
-def _compile(out_path: str, extra=()) -> bool:
+def _compile(out_path: str, extra=(), srcs=None) -> bool:
     """gcc the C oracle into out_path (OpenMP when available); returns whether OpenMP is
-    on. `extra` are additional compiler flags (the mutation tests pass a -D)."""
+    on. `extra` are additional compiler flags; `srcs` replaces the two C sources (the
+    mutation tests compile edited copies of them)."""
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         raise RuntimeError("no C compiler found to build the oracle")
     base = [cc, "-O2", "-fPIC", "-shared", "-std=c99", "-ffp-contract=off",
-            "-fno-fast-math", *extra, *_SRCS, "-o", out_path + ".tmp", "-lm"]
+            "-fno-fast-math", *extra, *(srcs or _SRCS), "-o", out_path + ".tmp", "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
                        capture_output=True, text=True)

@@ -50,19 +50,6 @@
 
 #define Q 9
 
-/* Planted mistakes, for the tests that check that each pin catches the mistake it is meant
- * to catch (tests/test_oracle_mutations.py builds a copy with one of them switched on).
- * The default build, and every result the oracle reports, has ORACLE_MUTATION = 0:
- *   1 the (v.u)^2 term of the equilibrium dropped
- *   2 transport pulling from x + v_j instead of x - v_j
- *   3 the transposed moment matrix in the definition stepper
- *   4 a wrong sign in block C3 of the shifting matrix
- *   5 relaxation rates applied to the wrong moments in the definition stepper
- *   6 s+ and s- swapped in the 2x2 block of Appendix B's cascade */
-#ifndef ORACLE_MUTATION
-#define ORACLE_MUTATION 0
-#endif
-
 /* Velocity set of Section 1.3 in the paper's order, in units of lambda. */
 static const int CX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int CY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -109,8 +96,7 @@ void orc_feq(double rho, double ux, double uy, double l, double* feq) {
     double uu = ux * ux + uy * uy;
     for (int j = 0; j < Q; ++j) {
         double vu = l * CX[j] * ux + l * CY[j] * uy;
-        const double quad = ORACLE_MUTATION == 1 ? 0.0 : 4.5 * vu * vu / (l2 * l2);
-        feq[j] = W[j] * rho * (1.0 + 3.0 * vu / l2 + quad - 1.5 * uu / l2);
+        feq[j] = W[j] * rho * (1.0 + 3.0 * vu / l2 + 4.5 * vu * vu / (l2 * l2) - 1.5 * uu / l2);
     }
 }
 
@@ -171,16 +157,14 @@ int orc_collide_definition(const double* f, double utx, double uty, double l,
     for (int k = 0; k < Q; ++k) {
         double a = 0.0, b = 0.0;
         for (int j = 0; j < Q; ++j) {
-            const double Mkj = ORACLE_MUTATION == 3 ? M[j * Q + k] : M[k * Q + j];
-            a += Mkj * f[j];
-            b += Mkj * feq[j];
+            a += M[k * Q + j] * f[j];
+            b += M[k * Q + j] * feq[j];
         }
         m[k] = a;
         meq[k] = b;
     }
     for (int k = 0; k < Q; ++k) {
-        const double sk = ORACLE_MUTATION == 5 ? s[(k + 1) % Q] : s[k];
-        ms[k] = m[k] + sk * (meq[k] - m[k]);
+        ms[k] = m[k] + s[k] * (meq[k] - m[k]);
     }
     return orc_lu_solve(M, ms, fstar);
 }
@@ -210,7 +194,7 @@ void orc_shift_matrix(double ux, double uy, double l, double* T) {
     T[6 * Q + 1] = 3.0 * (uu + 2.0 * ux * ux) / l3;  T[6 * Q + 2] = 6.0 * ux * uy / l3;
     T[7 * Q + 1] = 6.0 * ux * uy / l3;               T[7 * Q + 2] = 3.0 * (uu + 2.0 * uy * uy) / l3;
     /* C3 */
-    T[6 * Q + 3] = -2.0 * ux / l;  T[6 * Q + 4] = (ORACLE_MUTATION == 4 ? 3.0 : -3.0) * ux / l;
+    T[6 * Q + 3] = -2.0 * ux / l;  T[6 * Q + 4] = -3.0 * ux / l;
     T[6 * Q + 5] = -6.0 * uy / l;
     T[7 * Q + 3] = -2.0 * uy / l;  T[7 * Q + 4] = 3.0 * uy / l;   T[7 * Q + 5] = -6.0 * ux / l;
     /* D1 */
@@ -403,9 +387,8 @@ void orc_stream(int64_t nx, int64_t ny, const double* fin, double* fout, int nth
     for (int64_t y = 0; y < ny; ++y) {
         for (int64_t x = 0; x < nx; ++x) {
             for (int j = 0; j < Q; ++j) {
-                const int sgn = ORACLE_MUTATION == 2 ? -1 : 1;
-                int64_t xs = ((x - sgn * CX[j]) % nx + nx) % nx;
-                int64_t ys = ((y - sgn * CY[j]) % ny + ny) % ny;
+                int64_t xs = ((x - CX[j]) % nx + nx) % nx;
+                int64_t ys = ((y - CY[j]) % ny + ny) % ny;
                 fout[j * n + y * nx + x] = fin[j * n + ys * nx + xs];
             }
         }
@@ -506,16 +489,14 @@ int orc_collide_geier(const double* f, double utx, double uty, double l, const d
     for (int k = 0; k < Q; ++k) {
         double a = 0.0, b = 0.0;
         for (int j = 0; j < Q; ++j) {
-            const double Mkj = ORACLE_MUTATION == 3 ? M[j * Q + k] : M[k * Q + j];
-            a += Mkj * f[j];
-            b += Mkj * feq[j];
+            a += M[k * Q + j] * f[j];
+            b += M[k * Q + j] * feq[j];
         }
         m[k] = a;
         meq[k] = b;
     }
     for (int k = 0; k < Q; ++k) {
-        const double sk = ORACLE_MUTATION == 5 ? s[(k + 1) % Q] : s[k];
-        ms[k] = m[k] + sk * (meq[k] - m[k]);
+        ms[k] = m[k] + s[k] * (meq[k] - m[k]);
     }
     return orc_lu_solve(M, ms, fstar);
 }
@@ -567,12 +548,7 @@ int orc_collide_cascaded(const double* f, double l, const double* s, double* fst
         meq[k] = b;
     }
     /* right-hand side Lambda (m_eq - m) */
-    double sp = 0.5 * (s[3] + s[4]), sm = 0.5 * (s[3] - s[4]);
-    if (ORACLE_MUTATION == 6) {
-        const double t = sp;
-        sp = sm;
-        sm = t;
-    }
+    const double sp = 0.5 * (s[3] + s[4]), sm = 0.5 * (s[3] - s[4]);
     double rhs[Q];
     for (int k = 0; k < Q; ++k) rhs[k] = 0.0;
     rhs[3] = sp * (meq[3] - m[3]) + sm * (meq[4] - m[4]);

@@ -30,14 +30,6 @@
 
 #define Q3 19
 
-/* Planted mistakes for the pin-sensitivity tests (see lbmrv_oracle.c); off by default:
- *   7 the edge weight of the equilibrium 1/18 instead of 1/36
- *   8 the basis polynomial ZY^2 written as YZ^2 (a repeated row)
- *   9 transport pulling from z + v_z */
-#ifndef ORACLE_MUTATION
-#define ORACLE_MUTATION 0
-#endif
-
 static const int CX3[Q3] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 static const int CY3[Q3] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 static const int CZ3[Q3] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
@@ -69,7 +61,7 @@ double orc3_poly(int k, double X, double Y, double Z, double l) {
         case 12: return Y * X * X / l3;
         case 13: return Y * Z * Z / l3;
         case 14: return Z * X * X / l3;
-        case 15: return (ORACLE_MUTATION == 8 ? Y * Z * Z : Z * Y * Y) / l3;
+        case 15: return Z * Y * Y / l3;
         case 16: return X * X * Y * Y / l4;
         case 17: return X * X * Z * Z / l4;
         case 18: return Y * Y * Z * Z / l4;
@@ -89,7 +81,7 @@ void orc3_feq(double rho, double ux, double uy, double uz, double l, double* feq
     for (int j = 0; j < Q3; ++j) {
         int nnz = (CX3[j] != 0) + (CY3[j] != 0) + (CZ3[j] != 0);
         double w = nnz == 0 ? 1.0 / 3.0
-                            : (nnz == 1 || ORACLE_MUTATION == 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+                            : (nnz == 1 ? 1.0 / 18.0 : 1.0 / 36.0);
         double vu = l * (CX3[j] * ux + CY3[j] * uy + CZ3[j] * uz);
         feq[j] = w * rho * (1.0 + 3.0 * vu / l2 + 4.5 * vu * vu / (l2 * l2) - 1.5 * uu / l2);
     }
@@ -197,8 +189,7 @@ void orc3_stream(int64_t nx, int64_t ny, int64_t nz, const double* fin, double* 
                 for (int j = 0; j < Q3; ++j) {
                     int64_t xs = ((x - CX3[j]) % nx + nx) % nx;
                     int64_t ys = ((y - CY3[j]) % ny + ny) % ny;
-                    const int sz = ORACLE_MUTATION == 9 ? -1 : 1;
-                    int64_t zs = ((z - sz * CZ3[j]) % nz + nz) % nz;
+                    int64_t zs = ((z - CZ3[j]) % nz + nz) % nz;
                     fout[j * n + (z * ny + y) * nx + x] = fin[j * n + (zs * ny + ys) * nx + xs];
                 }
 }
