@@ -328,12 +328,12 @@ def gpu_arm(args):
             extras["relative_u_prescribed_stored_field"] = side_measure(
                 torch, D2Q9, inp, "fp32", "prescribed", L, fields, k, peak, stored_field=True)
             # perturbed uniform flow U = (0.05, 0.02); 16-bit storage relative to the
-            # equilibrium at U (the form that meets the 2e-3 velocity bar)
+            # library's automatic reference (the mean flow of the initial fields), the
+            # default form, which meets the 2e-3 velocity bar on this workload
             big = inp.perturbed_uniform(8192, 8192, seed=0)
             for st in ("fp16", "bf16"):
                 extras[f"precision_{st}_8192"] = side_measure(torch, D2Q9, inp, st, "fluid",
-                                                              8192, big, k, peak,
-                                                              u_ref=(0.05, 0.02))
+                                                              8192, big, k, peak)
             extras["fp32_fluid_8192"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", 8192,
                                                      big, k, peak)
             del big

@@ -37,10 +37,14 @@
  *     floats (d = 2 or 3).
  *   - Stored value: g_j = f_j - f_eq,j(rho_ref, U_ref), the deviation from the equilibrium
  *     of a reference state, in the storage type of the handle (FP32, FP16 or BF16,
- *     round-to-nearest-even). By default U_ref = 0, so g_j = f_j - w_j rho_ref with
- *     w = (4/9, 1/9 x4, 1/36 x4); rho_ref = 0 stores f itself. lbmrv_set_reference sets a
- *     reference velocity (useful for 16-bit storage of a flow with a mean velocity). All
- *     arithmetic is FP32.
+ *     round-to-nearest-even). rho_ref is given at lbmrv_create (0 stores f itself when
+ *     U_ref = 0). By default U_ref is chosen automatically by each lbmrv_init_equilibrium:
+ *     the mean flow sum(rho u) / sum(rho) of its fields, which the periodic scheme
+ *     conserves (relation (rhoq) summed over the lattice), so the stored deviations stay
+ *     those of the perturbations around the mean flow and 16-bit rounding stays small.
+ *     lbmrv_set_reference fixes U_ref instead (U_ref = 0 is the plain form
+ *     g_j = f_j - w_j rho_ref, w = (4/9, 1/9 x4, 1/36 x4)); lbmrv_get_reference reports
+ *     it. All arithmetic is FP32.
  *   - The state kept by the handle after k steps is the POST-relaxation state
  *     S_k = C_k(f(k)) at time k: one lbmrv_step pulls the neighbours' S_{k-1}
  *     (transport) and relaxes at time k. Moments (rho, q) of S_k equal those of f(k),
@@ -116,7 +120,9 @@ LBMRV_API int64_t lbmrv_state_bytes(int lattice, const int64_t dims[3], int stor
  *   s        q relaxation rates in basis order: for D2Q9 the moment order of relation
  *            (mom): rho, q_x, q_y, e, p_xx, p_xy, q_x(3rd), q_y(3rd), eps; for the other
  *            lattices the order of their bases above. The 1 + d conserved rates must be 0
- *            (Section 1.1); the others are finite.
+ *            (Section 1.1); the others are finite. A rate outside (0, 2) is accepted with
+ *            a warning in lbmrv_last_error (of the handle, and of NULL on this thread):
+ *            that moment is then not damped (0 or 2) or amplified.
  *   umode    LBMRV_UT_* (prescribed mode: see lbmrv_set_utilde; default A = 0).
  *   storage  LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16.
  *   rho_ref  reference density of the stored deviation g = f - w rho_ref (0 stores f).
@@ -135,16 +141,29 @@ LBMRV_API int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], dou
 /* Release the handle and whatever it allocated. Synchronises its stream. NULL is a no-op. */
 LBMRV_API int lbmrv_destroy(lbmrv_t h);
 
-/* Message of the last failure on h, or of the last failed lbmrv_create on this thread
- * when h is NULL. Valid until the next call on h. */
+/* Message of the last failure (or rate warning) on h, or of the last failed (or warned)
+ * lbmrv_create on this thread when h is NULL. Valid until the next call on h. */
 LBMRV_API const char* lbmrv_last_error(lbmrv_t h);
 
-/* Reference state of the stored deviations: g = f - f_eq(rho_ref, u_ref), u_ref = d
- * doubles in physical units (NULL: zero). Changes how the stored state is read and written, so call it before
- * lbmrv_init_equilibrium / lbmrv_set_state; an existing state is not converted. The
- * default is (rho_ref of lbmrv_create, 0, 0). With 16-bit storage a reference velocity
- * near the mean flow keeps the stored deviations small and their rounding error with them. */
+/* Fixed reference state of the stored deviations: g = f - f_eq(rho_ref, u_ref), u_ref = d
+ * doubles in physical units (NULL: zero, the plain form g = f - w rho_ref). It turns the
+ * automatic choice off. It changes how the stored state is read and written, so call it
+ * before lbmrv_init_equilibrium / lbmrv_set_state; an existing state is not converted.
+ * Errors: LBMRV_E_INVAL (NULL handle, non-finite values). */
 LBMRV_API int lbmrv_set_reference(lbmrv_t h, double rho_ref, const double* u_ref);
+
+/* Automatic reference velocity (the default): from now on each lbmrv_init_equilibrium[_host]
+ * sets U_ref to the mean flow sum(rho u) / sum(rho) of its fields (an FP64 reduction on the
+ * device) before it builds the state, and rho_ref to the value given here. The mean flow
+ * is an invariant of the periodic scheme (total mass and momentum are conserved), so it
+ * remains the mean flow of every later state. lbmrv_set_state keeps the current
+ * reference. Errors: LBMRV_E_INVAL (NULL handle, rho_ref not finite). */
+LBMRV_API int lbmrv_set_reference_auto(lbmrv_t h, double rho_ref);
+
+/* Current reference state: *rho_ref_out and u_ref_out[0..2] (physical units, unused
+ * components 0); either pointer may be NULL. Returns 1 when the automatic choice is on,
+ * 0 when the reference is fixed, LBMRV_E_INVAL for a NULL handle. */
+LBMRV_API int lbmrv_get_reference(lbmrv_t h, double* rho_ref_out, double* u_ref_out);
 
 /* Change the stream later work is enqueued on. */
 LBMRV_API int lbmrv_set_stream(lbmrv_t h, void* stream);
@@ -173,13 +192,19 @@ LBMRV_API int lbmrv_set_utilde(lbmrv_t h, const float* ut0_dev, double amplitude
  * of u~, Section 1.2). f_eq is a fixed point of the relaxation for every u~, so it is
  * also the post-relaxation state at time 0.
  *   rho_dev  device FP32 [n], or NULL for rho = 1 everywhere.
- *   u_dev    device FP32 [d][n] (one plane per component), physical units. */
+ *   u_dev    device FP32 [d][n] (one plane per component), physical units.
+ * With the automatic reference (the default, lbmrv_set_reference_auto) the call first
+ * reduces the fields to their mean flow on the device and reads it back, so it
+ * synchronises the handle's stream; with a fixed reference it is asynchronous.
+ * Errors: LBMRV_E_INVAL; LBMRV_E_NONFINITE when the automatic reference meets non-finite
+ * fields (the state is then left unchanged); LBMRV_E_CUDA. */
 LBMRV_API int lbmrv_init_equilibrium(lbmrv_t h, const float* rho_dev, const float* u_dev);
 
 /* Same from host buffers: copies them into the non-current state buffer on the
  * handle's stream (no allocation), then builds the equilibrium. Pinned host memory is
- * faster; the call returns once the copies are enqueued and the host buffers may be
- * reused only after the stream has synchronised. */
+ * faster. With a fixed reference the call returns once the work is enqueued, and the host
+ * buffers may be reused only after the stream has synchronised; with the automatic
+ * reference it synchronises once the fields are on the device. */
 LBMRV_API int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u_host);
 
 /* Advance n >= 0 time steps. Each step is one fused kernel: pull transport of the
@@ -230,7 +255,8 @@ LBMRV_API int lbmrv_state_ptr(lbmrv_t h, void** ptr_out);
 /* Time index of the current state (number of steps since the last init/set_state). */
 LBMRV_API int64_t lbmrv_time(lbmrv_t h);
 
-/* Replace the 9 relaxation rates (same rules as lbmrv_create); applies to later steps. */
+/* Replace the q relaxation rates (same rules and warning as lbmrv_create); applies to
+ * later steps. */
 LBMRV_API int lbmrv_set_rates(lbmrv_t h, const double* s);
 
 /* ---------------------------------------------------------------- discrete adjoint
@@ -301,12 +327,16 @@ LBMRV_API int lbmrv_equilibrium_vjp(lbmrv_t h, const float* rho_dev, const float
  *   storage    LBMRV_FP32 / LBMRV_FP16 / LBMRV_BF16; rho_ref the stored offset (the
  *              state is read with a zero reference velocity; for a state stored with
  *              lbmrv_set_reference(rho_ref, U), add nx*ny*rho_ref*U to the momentum sums).
- *   dims       {nx, ny, 1}; nx*ny must be below 2^31 (larger sizes: LBMRV_E_INVAL).
+ *   dims       {nx, ny, 1} (any other depth: LBMRV_E_INVAL); nx*ny must be below 2^31
+ *              (larger sizes: LBMRV_E_INVAL).
  *   out_dev    4 device doubles: sum rho, sum q_x, sum q_y, non-finite node count.
  *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream).
  * Asynchronous; allocates nothing (no cudaMalloc, no cudaFree). The first call on a
  * device looks up the scratch array's device address (cudaGetSymbolAddress), so make
- * that first call before any stream capture. Every call shares the one scratch array:
+ * that first call before any stream capture. The address is kept per device and looked
+ * up again when the device's context has changed (after cudaDeviceReset, for example);
+ * make the first call after such a reset before any stream capture too. Every call
+ * shares the one scratch array:
  * calls that overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller. Each call overwrites all the scratch it reads, so nothing
  * needs clearing. Returns LBMRV_OK, LBMRV_E_INVAL or LBMRV_E_CUDA (no message is kept,

@@ -142,3 +142,13 @@ def random_flow_3d(nx: int, ny: int, nz: int, seed: int = 0, amp: float = 0.04,
                   amp * np.sin(TWO_PI * z / nz) + u_noise * noise[1],
                   amp * np.sin(TWO_PI * x / nx) + u_noise * noise[2]])
     return {"rho": rho, "u": u}
+
+
+def perturbed_uniform_3d(nx: int, ny: int, nz: int, seed: int = 0, U=(0.05, 0.02, 0.01),
+                         drho: float = 1e-3, du: float = 1e-3, rho0: float = 1.0):
+    """Randomly perturbed uniform 3D flow: rho = rho0 + drho N(0,1), u = U + du N(0,1) per
+    component (draws: rho, u_x, u_y, u_z). Returns rho (nz, ny, nx) and u (3, nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    rho = rho0 + drho * rng.standard_normal((nz, ny, nx))
+    u = np.stack([U[a] + du * rng.standard_normal((nz, ny, nx)) for a in range(3)])
+    return {"rho": rho, "u": u}

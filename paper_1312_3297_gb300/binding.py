@@ -66,6 +66,8 @@ SIGNATURES = [
     ("lbmrv_conserved_noalloc", _I, [_VP, _I, _I64P, _D, _D, _VP, _VP]),
     ("lbmrv_set_rates", _I, [_VP, _DP]),
     ("lbmrv_set_reference", _I, [_VP, _D, _DP]),
+    ("lbmrv_set_reference_auto", _I, [_VP, _D]),
+    ("lbmrv_get_reference", _I, [_VP, _DP, _DP]),
     ("lbmrv_conserved3", _I, [_VP, _DP]),
     ("lbmrv_step_conserved", _I, [_VP, _I64, _DP]),
     ("lbmrv_adjoint_workspace_bytes", _I64, [_VP, _I64, _I64]),
@@ -226,9 +228,34 @@ def lbmrv_time(h) -> int:
     return load().lbmrv_time(h)
 
 
+_STORAGE_BYTES = {LBMRV_FP32: 4, LBMRV_FP16: 2, LBMRV_BF16: 2}
+
+
+def _check_noalloc_tensors(state, storage, dims, out):
+    """No handle stands between the caller and the kernel here, so the tensors are checked
+    before the call: the state must hold 9 planes of nx*ny values of the storage type and
+    ``out`` 4 doubles, both on the current CUDA device."""
+    import torch
+
+    d = list(dims) + [1] * (3 - len(dims))
+    need = 9 * int(d[0]) * int(d[1]) * _STORAGE_BYTES.get(int(storage), 0)
+    if torch.is_tensor(state):
+        if not state.is_cuda or state.device.index != torch.cuda.current_device():
+            raise ValueError("state must be on the current CUDA device")
+        if state.numel() * state.element_size() < need:
+            raise ValueError(f"state holds fewer than the {need} bytes of 9 x {d[0]} x {d[1]} "
+                             "values of the storage type")
+    if torch.is_tensor(out):
+        if not out.is_cuda or out.device.index != torch.cuda.current_device():
+            raise ValueError("out must be on the current CUDA device")
+        if out.dtype != torch.float64 or out.numel() < 4:
+            raise ValueError("out must hold at least 4 float64 values")
+
+
 def lbmrv_conserved_noalloc(state, storage: int, dims, lam: float, rho_ref: float, out,
                             stream=None) -> None:
     """Sums of a caller-owned state into ``out`` (4 device doubles) without allocating."""
+    _check_noalloc_tensors(state, storage, dims, out)
     rc = load().lbmrv_conserved_noalloc(_addr(state), int(storage), _dims(dims), float(lam),
                                         float(rho_ref), _addr(out), _stream(stream))
     if rc < 0:
@@ -243,6 +270,18 @@ def lbmrv_set_rates(h, s) -> None:
 def lbmrv_set_reference(h, rho_ref: float, u_ref) -> None:
     u = (ctypes.c_double * 3)(*([float(v) for v in u_ref] + [0.0] * (3 - len(u_ref))))
     _check(load().lbmrv_set_reference(h, float(rho_ref), u), h)
+
+
+def lbmrv_set_reference_auto(h, rho_ref: float) -> None:
+    _check(load().lbmrv_set_reference_auto(h, float(rho_ref)), h)
+
+
+def lbmrv_get_reference(h):
+    """Returns (rho_ref, (u_x, u_y, u_z), automatic)."""
+    r = ctypes.c_double()
+    u = (ctypes.c_double * 3)()
+    rc = _check(load().lbmrv_get_reference(h, ctypes.byref(r), u), h)
+    return r.value, tuple(u), bool(rc)
 
 
 def lbmrv_conserved3(h, allow_nonfinite: bool = False):

@@ -341,6 +341,25 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_final(const double
     }
 }
 
+// FP64 sums of rho, rho u_x, rho u_y and rho u_z (0 when dim = 2) over initial fields:
+// the total mass and momentum of the equilibrium state built from them (relation (rhoq)
+// summed over the lattice; sum_j v_j f_eq,j = rho u at every node). rho may be NULL
+// (rho = 1); u holds dim planes of n values.
+__global__ void __launch_bounds__(kReduceThreads) k_mean_flow_partial(
+    const float* __restrict__ rho, const float* __restrict__ u, int64_t n, int dim,
+    double* __restrict__ part) {
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double r = rho ? (double)rho[i] : 1.0;
+        v[0] += r;
+        v[1] += r * (double)u[i];
+        v[2] += r * (double)u[n + i];
+        if (dim == 3) v[3] += r * (double)u[2 * n + i];
+    }
+    block_sum4<kReduceThreads>(v, part + 4 * (int64_t)blockIdx.x);
+}
+
 // Block b adds partials [256 b, 256 b + 256) of 4 doubles each into out[4 b].
 __global__ void __launch_bounds__(kReduceThreads) k_sum_partials(const double* __restrict__ part,
                                                                  int64_t nblk,
@@ -553,6 +572,15 @@ cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, i
 int conserved_blocks(int64_t n) {
     int64_t b = (n + kReduceThreads - 1) / kReduceThreads;
     return (int)(b < 1 ? 1 : (b > kReduceMaxBlocks ? kReduceMaxBlocks : b));
+}
+
+cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int dim,
+                             double* partials, int nblk, double* out, cudaStream_t st) {
+    k_mean_flow_partial<<<nblk, kReduceThreads, 0, st>>>(rho, u, n, dim, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_conserved_final<<<1, kReduceThreads, 0, st>>>(partials, nblk, 0.0, 0.0, 0.0, 1.0, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho_ref,

@@ -24,6 +24,7 @@ struct lbmrv_s {
     int64_t nx = 0, ny = 0, nz = 1, n = 0;
     double lambda = 1.0, rho_ref = 0.0;
     double u_ref[3] = {0.0, 0.0, 0.0};  // reference velocity of the stored deviations
+    bool ref_auto = true;  // u_ref := mean flow of the fields of each init_equilibrium
     double s[19] = {0};
     cudaStream_t stream = nullptr;
     void* f[2] = {nullptr, nullptr};

@@ -54,6 +54,11 @@ cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho
                              double jx_ref, double jy_ref, double lambda, double* partials,
                              int nblk, double* out, cudaStream_t st);
 
+// Sums {rho, rho u_x, rho u_y, rho u_z} of initial fields (rho NULL: 1; u: dim planes of n
+// floats) into out[4] (device); partials: 4 * nblk doubles of scratch.
+cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int dim,
+                             double* partials, int nblk, double* out, cudaStream_t st);
+
 // ---------------------------------------------------------------- D3Q19
 int step3_vector_width(int storage, int nx);
 cudaError_t launch_step3(int storage, int um, int nv, const void* src, void* dst,

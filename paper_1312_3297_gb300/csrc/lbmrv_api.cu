@@ -38,7 +38,44 @@ int check_rates(lbmrv_t h, int lattice, const double* s, const char* who) {
         if (!std::isfinite(s[k])) return fail(h, LBMRV_E_INVAL, "%s: s[%d] is not finite", who, k);
     return LBMRV_OK;
 }
+
+// A rate outside (0, 2) is accepted, with a warning in the last-error message: the
+// relaxation multiplies a moment's distance to equilibrium by 1 - s per step, so s = 0 or
+// 2 leaves that moment undamped and s < 0 or s > 2 amplifies it (Section 1.1).
+void warn_rates(lbmrv_t h, int lattice, const double* s, const char* who) {
+    const int q = lattice_q(lattice), nc = 1 + lattice_dim(lattice);
+    for (int k = nc; k < q; ++k)
+        if (!(s[k] > 0.0 && s[k] < 2.0)) {
+            fail(h, LBMRV_OK, "%s: warning: s[%d] = %g is outside (0, 2); that moment is %s",
+                 who, k, s[k], (s[k] == 0.0 || s[k] == 2.0) ? "not damped" : "amplified");
+            return;
+        }
+}
 }  // namespace
+
+// The automatic reference velocity: U_ref = sum rho u / sum rho over the fields an
+// equilibrium is about to be built from (an FP64 device reduction, read back on the host).
+// Total mass and momentum are invariants of the periodic scheme (relation (rhoq) summed
+// over the lattice: relaxation conserves them at every node, transport moves them), so
+// U_ref stays the mean flow of the whole run. Synchronises the handle's stream.
+int apply_auto_reference(lbmrv_t h, const float* rho, const float* u, const char* who) {
+    if (!h->ref_auto) return LBMRV_OK;
+    double* res = h->red + 8 * (size_t)h->red_blocks;
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};
+    cudaError_t e = launch_mean_flow(rho, u, h->n, h->dim, h->red, h->red_blocks, res,
+                                     h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sums, res, sizeof(sums), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, who);
+    for (int c = 0; c < 4; ++c)
+        if (!std::isfinite(sums[c]))
+            return fail(h, LBMRV_E_NONFINITE, "%s: the fields hold non-finite values", who);
+    if (!(sums[0] > 0.0))
+        return fail(h, LBMRV_E_INVAL, "%s: the total mass must be positive", who);
+    for (int a = 0; a < 3; ++a) h->u_ref[a] = a < h->dim ? sums[1 + a] / sums[0] : 0.0;
+    return LBMRV_OK;
+}
 
 int fail(lbmrv_t h, int code, const char* fmt, ...) {
     char* buf = h ? h->err : g_create_err;
@@ -172,6 +209,8 @@ int lbmrv_create(lbmrv_t* out, int lattice, const int64_t dims[3], double lambda
         return fail(nullptr, LBMRV_E_NOMEM, "lbmrv_create: device allocation of %zu bytes failed",
                     2 * bytes);
     }
+    warn_rates(h, lattice, s, "lbmrv_create");
+    warn_rates(nullptr, lattice, s, "lbmrv_create");
     *out = h;
     return LBMRV_OK;
 }
@@ -222,6 +261,7 @@ int lbmrv_set_rates(lbmrv_t h, const double* s) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_rates: NULL handle");
     int rc = check_rates(h, h->lattice, s, "lbmrv_set_rates");
     if (rc != LBMRV_OK) return rc;
+    warn_rates(h, h->lattice, s, "lbmrv_set_rates");
     for (int k = 0; k < h->q; ++k) h->s[k] = s[k];
     return LBMRV_OK;
 }
@@ -235,7 +275,25 @@ int lbmrv_set_reference(lbmrv_t h, double rho_ref, const double* u_ref) {
         return fail(h, LBMRV_E_INVAL, "lbmrv_set_reference: values must be finite");
     h->rho_ref = rho_ref;
     for (int a = 0; a < 3; ++a) h->u_ref[a] = u[a];
+    h->ref_auto = false;
     return LBMRV_OK;
+}
+
+int lbmrv_set_reference_auto(lbmrv_t h, double rho_ref) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_set_reference_auto: NULL handle");
+    if (!std::isfinite(rho_ref))
+        return fail(h, LBMRV_E_INVAL, "lbmrv_set_reference_auto: rho_ref is not finite");
+    h->rho_ref = rho_ref;
+    h->ref_auto = true;
+    return LBMRV_OK;
+}
+
+int lbmrv_get_reference(lbmrv_t h, double* rho_ref, double* u_ref) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_get_reference: NULL handle");
+    if (rho_ref) *rho_ref = h->rho_ref;
+    if (u_ref)
+        for (int a = 0; a < 3; ++a) u_ref[a] = h->u_ref[a];
+    return h->ref_auto ? 1 : 0;
 }
 
 int lbmrv_set_utilde(lbmrv_t h, const float* ut0_dev, double amplitude, double period) {
@@ -254,6 +312,8 @@ int lbmrv_init_equilibrium(lbmrv_t h, const float* rho_dev, const float* u_dev) 
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_init_equilibrium: NULL handle");
     if (!u_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_init_equilibrium: u is NULL");
     DeviceGuard g(h->device);
+    int rc = apply_auto_reference(h, rho_dev, u_dev, "lbmrv_init_equilibrium");
+    if (rc != LBMRV_OK) return rc;
     cudaError_t e;
     if (h->dim == 2)
         e = launch_init_eq(h->storage, h->f[h->cur], rho_dev, u_dev, h->n, store_ref(h),
@@ -279,6 +339,8 @@ int lbmrv_init_equilibrium_host(lbmrv_t h, const float* rho_host, const float* u
         e = cudaMemcpyAsync(stage + h->n, u_host, h->dim * nb, cudaMemcpyHostToDevice, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_init_equilibrium_host: copy");
     const float* rho = rho_host ? stage : nullptr;
+    int rc = apply_auto_reference(h, rho, stage + h->n, "lbmrv_init_equilibrium_host");
+    if (rc != LBMRV_OK) return rc;
     if (h->dim == 2)
         e = launch_init_eq(h->storage, h->f[h->cur], rho, stage + h->n, h->n, store_ref(h),
                            (float)(1.0 / h->lambda), h->stream, h->basis);

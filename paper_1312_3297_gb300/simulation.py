@@ -15,7 +15,6 @@ _MODES = {"zero": B.LBMRV_UT_ZERO, "fluid": B.LBMRV_UT_FLUID,
 _STORAGES = {"fp32": B.LBMRV_FP32, "fp16": B.LBMRV_FP16, "bf16": B.LBMRV_BF16}
 STORAGE_DTYPES = {B.LBMRV_FP32: torch.float32, B.LBMRV_FP16: torch.float16,
                   B.LBMRV_BF16: torch.bfloat16}
-WEIGHTS = (4 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 9, 1 / 36, 1 / 36, 1 / 36, 1 / 36)
 
 
 def mode_id(mode) -> int:
@@ -27,7 +26,11 @@ def storage_id(storage) -> int:
 
 
 class D2Q9:
-    """A periodic nx x ny D2Q9 lattice advanced by the relative-velocity scheme."""
+    """A periodic nx x ny D2Q9 lattice advanced by the relative-velocity scheme.
+
+    The stored state is g = f - f_eq(rho_ref, u_ref). With ``u_ref=None`` (the default)
+    the library sets u_ref at each init_equilibrium to the mean flow of the fields it is
+    given; a tuple fixes it ((0, 0) is the plain form g = f - w rho_ref)."""
 
     LATTICE = B.LBMRV_D2Q9
     Q = 9
@@ -57,9 +60,8 @@ class D2Q9:
             self.h = B.lbmrv_create(self.LATTICE, dims, self.lam, list(s), self.mode,
                                     self.storage, self.rho_ref, self.stream,
                                     self._bufs[0], self._bufs[1])
-        self.u_ref = tuple(float(v) for v in (u_ref or (0.0,) * self.DIM))
-        if any(v != 0.0 for v in self.u_ref):
-            B.lbmrv_set_reference(self.h, self.rho_ref, self.u_ref)
+        if u_ref is not None:
+            B.lbmrv_set_reference(self.h, self.rho_ref, tuple(float(v) for v in u_ref))
         self._ut0 = None
         self.s = [float(v) for v in s]
         self.amp, self.period = 0.0, 0.0
@@ -99,6 +101,22 @@ class D2Q9:
         self.close()
 
     # -- configuration
+    @property
+    def u_ref(self) -> tuple:
+        """Reference velocity of the stored deviations (d components, physical units)."""
+        return B.lbmrv_get_reference(self.h)[1][:self.DIM]
+
+    def set_reference(self, rho_ref: float, u_ref):
+        """Fix the reference state (turns the automatic choice off)."""
+        B.lbmrv_set_reference(self.h, rho_ref, tuple(float(v) for v in u_ref))
+        self.rho_ref = float(rho_ref)
+
+    def set_reference_auto(self, rho_ref: float | None = None):
+        """Let each init_equilibrium take u_ref from the mean flow of its fields."""
+        if rho_ref is not None:
+            self.rho_ref = float(rho_ref)
+        B.lbmrv_set_reference_auto(self.h, self.rho_ref)
+
     def set_kernel_width(self, nodes_per_thread: int):
         B.lbmrv_set_kernel_width(self.h, nodes_per_thread)
 

@@ -35,7 +35,9 @@ def product_populations(rho_ref, u_ref, lam=1.0):
 
 
 def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=None,
-            ut0=None, amp=0.0, period=0.0, width=0, u_ref=(0.0, 0.0), cascaded=False):
+            ut0=None, amp=0.0, period=0.0, width=0, u_ref=None, cascaded=False):
+    """u_ref=None: the library's automatic reference (the mean flow of the fields); a
+    tuple fixes it. Populations are rebuilt from the reference the handle reports."""
     import torch
 
     from paper_1312_3297_gb300 import D2Q9, D2Q9Cascaded
@@ -52,7 +54,7 @@ def gpu_run(nx, ny, s, mode, steps, fields, storage="fp32", lam=1.0, rho_ref=Non
     sim.step(steps)
     g = sim.state().double().cpu().numpy()
     ref_pop = product_populations if cascaded else reference_populations
-    f = g + ref_pop(sim.rho_ref, u_ref, lam)[:, None, None]
+    f = g + ref_pop(sim.rho_ref, sim.u_ref, lam)[:, None, None]
     r, a, b = (t.double().cpu().numpy() for t in sim.moments())
     sim.close()
     return f, (r, a, b)
@@ -99,7 +101,7 @@ def oracle_kinetic_energy(rho0, u0, s, mode, steps, amp=0.0, period=0.0, ut0=Non
 
 
 def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=None,
-                  field_grad=False, u_ref=(0.0, 0.0)):
+                  field_grad=False, u_ref=None):
     """Kinetic energy after `steps` steps and its gradients from the CUDA adjoint:
     (L, dL/du0 [2, ny, nx], dL/ds [9], dL/dA, dL/du~0 or None)."""
     import torch
@@ -154,7 +156,7 @@ def gpu_run3(shape, s, mode, steps, rho, u, storage="fp32", ut0=None, amp=0.0, p
     sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in u))
     sim.step(steps)
     g = sim.state().double().cpu().numpy()
-    f = g + reference_populations3(sim.rho_ref, u_ref or (0, 0, 0))[:, None, None, None]
+    f = g + reference_populations3(sim.rho_ref, sim.u_ref)[:, None, None, None]
     m = [t.double().cpu().numpy() for t in sim.moments()]
     sim.close()
     return f, m[0], np.stack(m[1:])

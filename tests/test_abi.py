@@ -114,6 +114,47 @@ def test_null_handle_calls_fail_cleanly():
     B.lbmrv_destroy(None)
 
 
+def test_null_handle_reference_calls_fail_cleanly():
+    from paper_1312_3297_gb300 import binding as B
+
+    for fn, args in [(B.lbmrv_set_reference, (None, 1.0, (0.0, 0.0))),
+                     (B.lbmrv_set_reference_auto, (None, 1.0)),
+                     (B.lbmrv_get_reference, (None,))]:
+        with pytest.raises(B.LbmrvError) as ei:
+            fn(*args)
+        assert ei.value.status == B.LBMRV_E_INVAL
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("bad", [0.0, 2.0, 2.5, -0.3])
+def test_rates_outside_0_2_are_accepted_with_a_warning(bad):
+    """A non-conserved rate outside (0, 2) leaves its moment undamped or amplified; the
+    handle is created (or the rates replaced) and the last-error message holds a warning
+    naming the rate. Rates inside (0, 2) leave no warning."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1312_3297_gb300 import binding as B
+
+    s = list(S_OK)
+    s[7] = bad
+    h = B.lbmrv_create(0, (8, 8, 1), 1.0, s, 1, 0, 1.0)
+    try:
+        msg = B.lbmrv_last_error(h)
+        assert "warning" in msg and "s[7]" in msg, msg
+        assert "warning" in B.lbmrv_last_error(None)
+        B.lbmrv_set_rates(h, S_OK)
+        h2 = B.lbmrv_create(0, (8, 8, 1), 1.0, S_OK, 1, 0, 1.0)
+        assert "warning" not in B.lbmrv_last_error(h2)
+        s2 = list(S_OK)
+        s2[4] = bad
+        B.lbmrv_set_rates(h2, s2)
+        assert "s[4]" in B.lbmrv_last_error(h2)
+        B.lbmrv_destroy(h2)
+    finally:
+        B.lbmrv_destroy(h)
+
+
 def test_product_has_no_cpu_fallback():
     """The product package never imports the oracle and has no CPU compute path."""
     pkg = os.path.join(ROOT, "paper_1312_3297_gb300")

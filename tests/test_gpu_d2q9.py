@@ -10,7 +10,8 @@ import numpy as np
 import pytest
 
 import lbm_inputs as inp
-from pairs import S_PAPER, W, f32_fields, gpu_run, oracle_run, rel_errors
+from pairs import (S_PAPER, W, f32_fields, gpu_run, oracle_run, reference_populations,
+                   rel_errors)
 
 pytestmark = pytest.mark.gpu
 
@@ -252,7 +253,8 @@ def test_full_size_4096_sampled_parity(mode):
     errs = []
     for c in centers:
         ref = _window_oracle(fields, c, steps + 1, steps, s, mid, 0.03, 1000.0, L, L)
-        got = g[:, c[1], c[0]].double().cpu().numpy() + W * sim.rho_ref
+        got = g[:, c[1], c[0]].double().cpu().numpy() + reference_populations(
+            sim.rho_ref, sim.u_ref)
         errs.append(np.abs(got - ref).max())
         fmax = max(fmax, np.abs(ref).max())
     assert max(errs) / fmax <= TOL, errs
@@ -312,6 +314,69 @@ def test_conserved_sums_with_reference_velocity():
     np.testing.assert_allclose(c0[0], rho.sum(), rtol=1e-6)
     np.testing.assert_allclose(c0[1], (rho * ux).sum(), rtol=1e-5)
     np.testing.assert_allclose(c0[2], (rho * uy).sum(), rtol=1e-5)
+    sim.close()
+
+
+@pytest.mark.parametrize("lattice", ["d2q9", "cascaded", "d3q19"])
+def test_automatic_reference_is_the_mean_flow(lattice):
+    """By default each init_equilibrium stores deviations from f_eq(rho_ref, U) with U the
+    mean flow sum(rho u) / sum(rho) of its fields (FP64 on the device, against numpy here);
+    a fixed reference turns that off and the automatic choice can be turned back on. The
+    mean flow is conserved, so the stored state's momentum over its mass stays U."""
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9, D2Q9Cascaded, D3Q19
+
+    if lattice == "d3q19":
+        d = inp.random_flow_3d(24, 10, 6, seed=5)
+        rho = inp.to_f32_exact(d["rho"])
+        u = inp.to_f32_exact(d["u"] + np.array([0.03, -0.02, 0.01])[:, None, None, None])
+        sim = D3Q19(24, 10, 6, [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3,
+                    mode="fluid", storage="bf16")
+        comps = list(u)
+    else:
+        rho, ux, uy = f32_fields(inp.perturbed_uniform(40, 24, seed=6, U=(0.05, 0.02)))
+        cls = D2Q9Cascaded if lattice == "cascaded" else D2Q9
+        s = [0, 0, 0, 1.4, 1.9, 1.9, 1.2, 1.2, 1.4]
+        sim = cls(40, 24, s, mode="fluid", storage="fp16")
+        comps = [ux, uy]
+    want = np.array([(rho * c).sum() for c in comps]) / rho.sum()
+    assert B_ref_auto(sim)
+    sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in comps))
+    np.testing.assert_allclose(sim.u_ref, want, rtol=1e-12, atol=1e-15)
+    sim.step(7)
+    c = sim.conserved3()
+    np.testing.assert_allclose(np.array(c[1:1 + len(comps)]) / c[0], want, rtol=2e-3,
+                               atol=1e-6)
+    sim.set_reference(sim.rho_ref, [0.0] * len(comps))
+    assert not B_ref_auto(sim)
+    sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in comps))
+    assert tuple(sim.u_ref) == (0.0,) * len(comps)
+    sim.set_reference_auto()
+    assert B_ref_auto(sim)
+    sim.init_equilibrium(torch.as_tensor(rho), *(torch.as_tensor(c) for c in comps))
+    np.testing.assert_allclose(sim.u_ref, want, rtol=1e-12, atol=1e-15)
+    sim.close()
+
+
+def B_ref_auto(sim):
+    from paper_1312_3297_gb300 import binding as B
+
+    return B.lbmrv_get_reference(sim.h)[2]
+
+
+def test_automatic_reference_rejects_nonfinite_fields():
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9, binding as B
+
+    rho, ux, uy = f32_fields(inp.random_sine_flow(16, 8, seed=1))
+    ux = ux.copy()
+    ux[3, 4] = np.nan
+    sim = D2Q9(16, 8, S_PAPER, mode="fluid")
+    with pytest.raises(B.LbmrvError) as ei:
+        sim.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+    assert ei.value.status == B.LBMRV_E_NONFINITE
     sim.close()
 
 
