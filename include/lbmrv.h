@@ -317,6 +317,81 @@ LBMRV_API int lbmrv_equilibrium_vjp(lbmrv_t h, const float* rho_dev, const float
                                     const float* dL_dS0_dev, float* dL_drho_dev,
                                     float* dL_du_dev);
 
+/* ---------------------------------------------------------------- slab decomposition
+ * What is split across GPUs (or handles) is the exact transport of Section 1.1 (relation
+ * (transport)): in pull form a node reads population j from x - v_j dt, so each layer of the
+ * lattice (D2Q9: a row, the slab axis is y; D3Q19: a z-plane, the axis is z) needs from each
+ * neighbouring layer only the populations whose velocity crosses between them: 3 of 9 for
+ * D2Q9 (c_y = +-1), 5 of 19 for D3Q19 (c_z = +-1). A slab handle is an ordinary handle whose
+ * lattice has m = own layers + 2 layers: layers 1 .. m-2 are its own, layers 0 and m-1 are
+ * halo copies of the neighbours' edge layers. Each step: lbmrv_halo_pack, exchange the
+ * buffers with the neighbours (the caller's transport: a device copy, NCCL, ...),
+ * lbmrv_halo_unpack, lbmrv_step(h, 1). The step runs over the whole slab unchanged; what it
+ * computes in the halo layers is never read, since the next exchange overwrites every halo
+ * value a step reads. All slabs of one lattice must store relative to one reference
+ * (lbmrv_set_reference, e.g. lbmrv_set_reference_sums of the summed lbmrv_flow_sums).
+ * Face buffers hold lbmrv_halo_count values of the storage type; value b is the k-th
+ * crossing population (ascending population index), k = b / L, at in-layer node i = b % L
+ * (L = nx for D2Q9, nx*ny for D3Q19). */
+
+/* Partition of `extent` layers among `ranks` slabs: slab `rank` owns `*count` consecutive
+ * layers from global layer `*first`; the first (extent % ranks) slabs own one layer more.
+ * Host only. LBMRV_E_INVAL unless 1 <= ranks <= extent and 0 <= rank < ranks. */
+LBMRV_API int lbmrv_slab_plan(int64_t extent, int ranks, int rank, int64_t* first,
+                              int64_t* count);
+
+/* Values in one face buffer for a slab lattice of the given dims (halo layers included):
+ * 3*nx for D2Q9, 5*nx*ny for D3Q19; -1 when dims hold fewer than 3 layers. Host only. */
+LBMRV_API int64_t lbmrv_halo_count(int lattice, const int64_t dims[3]);
+
+/* Index maps of one face (side 0: the lower face, layers 0 and 1; side 1: the upper face,
+ * layers m-1 and m-2), as element offsets into the state (plane j at j*n, layout above), in
+ * buffer order, lbmrv_halo_count entries each (either pointer may be NULL):
+ *   send_idx  values lbmrv_halo_pack puts in the face's buffer: the edge layer's
+ *             populations moving across the face (c = -1 through the lower face, c = +1
+ *             through the upper face);
+ *   recv_idx  halo values lbmrv_halo_unpack fills from the buffer received across the
+ *             face (c = +1 into layer 0, c = -1 into layer m-1).
+ * The buffer a slab sends through its upper face is the one its upper neighbour receives
+ * through its lower face, and vice versa. Host only: these maps are the definition the
+ * device pack and unpack follow. LBMRV_E_INVAL for bad dims or side. */
+LBMRV_API int lbmrv_halo_map(int lattice, const int64_t dims[3], int side, int64_t* send_idx,
+                             int64_t* recv_idx);
+
+/* Declare h a slab: its own layers 1 .. m-2 are the global layers first .. first+m-3 of a
+ * periodic lattice of `extent` layers along the slab axis (0 <= first < extent, extent >=
+ * m-2). Effects: the analytic prescribed field (D2Q9) is evaluated at the global row;
+ * lbmrv_conserved[3] and lbmrv_step_conserved sum the own layers only (the latter by a
+ * separate pass); the automatic reference is turned off (a slab needs the shared reference,
+ * and lbmrv_init_equilibrium on a slab with the automatic reference is LBMRV_E_INVAL);
+ * lbmrv_moments still covers every layer; the adjoint entry points and
+ * lbmrv_kinetic_energy return LBMRV_E_UNSUPPORTED. LBMRV_E_INVAL for fewer than 3 layers. */
+LBMRV_API int lbmrv_set_slab(lbmrv_t h, int64_t first, int64_t extent);
+
+/* Pack the current state's outgoing face values: send_lo_dev for the neighbour below
+ * (side 0), send_hi_dev for the neighbour above (side 1), device buffers of
+ * lbmrv_halo_count values of the storage type, either may be NULL. Asynchronous on the
+ * handle's stream. LBMRV_E_INVAL when h is not a slab. */
+LBMRV_API int lbmrv_halo_pack(lbmrv_t h, void* send_lo_dev, void* send_hi_dev);
+
+/* Write received face values into the current state's halo layers: recv_lo_dev holds what
+ * the neighbour below packed for its upper face, recv_hi_dev what the neighbour above packed
+ * for its lower face (either may be NULL). Asynchronous. LBMRV_E_INVAL when h is not a
+ * slab. */
+LBMRV_API int lbmrv_halo_unpack(lbmrv_t h, const void* recv_lo_dev, const void* recv_hi_dev);
+
+/* FP64 sums {sum rho, sum rho u_x, sum rho u_y, sum rho u_z (0 for D2Q9)} of initial fields
+ * (laid out as for lbmrv_init_equilibrium; rho_dev NULL: 1) over the handle's own nodes (a
+ * slab's own layers). Summed over the slabs, they give the shared mean-flow reference.
+ * Synchronous. */
+LBMRV_API int lbmrv_flow_sums(lbmrv_t h, const float* rho_dev, const float* u_dev,
+                              double out_host[4]);
+
+/* lbmrv_set_reference(h, rho_ref, U) with U = sums[1..d] / sums[0] (sums as from
+ * lbmrv_flow_sums). LBMRV_E_INVAL when sums[0] <= 0, LBMRV_E_NONFINITE for non-finite
+ * sums. */
+LBMRV_API int lbmrv_set_reference_sums(lbmrv_t h, double rho_ref, const double sums[4]);
+
 /* The same sums as lbmrv_conserved for a caller-owned D2Q9 state, with no handle and no
  * device allocation. The paper has no counterpart: this exists for callers that cannot
  * allocate when they need the check (an allocator that owns all device memory, a loop

@@ -68,6 +68,14 @@ SIGNATURES = [
     ("lbmrv_set_reference", _I, [_VP, _D, _DP]),
     ("lbmrv_set_reference_auto", _I, [_VP, _D]),
     ("lbmrv_get_reference", _I, [_VP, _DP, _DP]),
+    ("lbmrv_slab_plan", _I, [_I64, _I, _I, _I64P, _I64P]),
+    ("lbmrv_halo_count", _I64, [_I, _I64P]),
+    ("lbmrv_halo_map", _I, [_I, _I64P, _I, _VP, _VP]),
+    ("lbmrv_set_slab", _I, [_VP, _I64, _I64]),
+    ("lbmrv_halo_pack", _I, [_VP, _VP, _VP]),
+    ("lbmrv_halo_unpack", _I, [_VP, _VP, _VP]),
+    ("lbmrv_flow_sums", _I, [_VP, _VP, _VP, _DP]),
+    ("lbmrv_set_reference_sums", _I, [_VP, _D, _DP]),
     ("lbmrv_conserved3", _I, [_VP, _DP]),
     ("lbmrv_step_conserved", _I, [_VP, _I64, _DP]),
     ("lbmrv_adjoint_workspace_bytes", _I64, [_VP, _I64, _I64]),
@@ -282,6 +290,59 @@ def lbmrv_get_reference(h):
     u = (ctypes.c_double * 3)()
     rc = _check(load().lbmrv_get_reference(h, ctypes.byref(r), u), h)
     return r.value, tuple(u), bool(rc)
+
+
+def lbmrv_slab_plan(extent: int, ranks: int, rank: int):
+    """Returns (first, count): the layers slab `rank` of `ranks` owns."""
+    first, count = ctypes.c_int64(), ctypes.c_int64()
+    rc = load().lbmrv_slab_plan(int(extent), int(ranks), int(rank), ctypes.byref(first),
+                                ctypes.byref(count))
+    if rc < 0:
+        raise LbmrvError(rc, f"lbmrv_slab_plan({extent}, {ranks}, {rank})")
+    return first.value, count.value
+
+
+def lbmrv_halo_count(lattice: int, dims) -> int:
+    return load().lbmrv_halo_count(int(lattice), _dims(dims))
+
+
+def lbmrv_halo_map(lattice: int, dims, side: int):
+    """Returns (send_idx, recv_idx) as numpy int64 arrays."""
+    import numpy as np
+
+    count = lbmrv_halo_count(lattice, dims)
+    if count < 0:
+        raise LbmrvError(LBMRV_E_INVAL, f"lbmrv_halo_count: bad slab dims {tuple(dims)}")
+    send = np.empty(count, dtype=np.int64)
+    recv = np.empty(count, dtype=np.int64)
+    rc = load().lbmrv_halo_map(int(lattice), _dims(dims), int(side), send.ctypes.data,
+                               recv.ctypes.data)
+    if rc < 0:
+        raise LbmrvError(rc, f"lbmrv_halo_map(side={side})")
+    return send, recv
+
+
+def lbmrv_set_slab(h, first: int, extent: int) -> None:
+    _check(load().lbmrv_set_slab(h, int(first), int(extent)), h)
+
+
+def lbmrv_halo_pack(h, send_lo, send_hi) -> None:
+    _check(load().lbmrv_halo_pack(h, _addr(send_lo), _addr(send_hi)), h)
+
+
+def lbmrv_halo_unpack(h, recv_lo, recv_hi) -> None:
+    _check(load().lbmrv_halo_unpack(h, _addr(recv_lo), _addr(recv_hi)), h)
+
+
+def lbmrv_flow_sums(h, rho, u):
+    out = (ctypes.c_double * 4)()
+    _check(load().lbmrv_flow_sums(h, _addr(rho), _addr(u), out), h)
+    return list(out)
+
+
+def lbmrv_set_reference_sums(h, rho_ref: float, sums) -> None:
+    sv = (ctypes.c_double * 4)(*[float(v) for v in sums])
+    _check(load().lbmrv_set_reference_sums(h, float(rho_ref), sv), h)
 
 
 def lbmrv_conserved3(h, allow_nonfinite: bool = False):

@@ -43,6 +43,7 @@ struct StepArgs {
     float amp_t;         // prescribed mode: A cos(2 pi t / P) / lambda at this step
     float two_over_nx;   // 2 / nx, 2 / ny for cospi/sinpi of the analytic field
     float two_over_ny;
+    int y_off;           // global row of local row y is y + y_off (a slab; else 0)
     const float* ut0;    // prescribed base field [2][n] or nullptr
     const float* sin_x;  // sin(2 pi x / nx), x < nx: y-component of the analytic field
 };
@@ -223,7 +224,7 @@ __device__ __forceinline__ void relative_velocity(const float g[9], const StoreR
         ux = (ref.jx + m.jx) * ir;
         uy = (ref.jy + m.jy) * ir;
     } else if (UM == UM_ANALYTIC) {
-        ux = a.amp_t * cospif(a.two_over_ny * (float)y);
+        ux = a.amp_t * cospif(a.two_over_ny * (float)(y + a.y_off));
         uy = a.amp_t * __ldg(a.sin_x + x);
     } else {
         const int64_t n = (int64_t)a.nx * a.ny;

@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
             // per-column table (one vector load per pack, served by L1/L2)
             float ux_row = 0.0f, sx[NV];
             if (UM == UM_ANALYTIC) {
-                ux_row = a.amp_t * cospif(a.two_over_ny * (float)y);
+                ux_row = a.amp_t * cospif(a.two_over_ny * (float)(y + a.y_off));
                 load_pack<float, NV>(a.sin_x + p.x0, true, sx);
             }
             if constexpr (BASIS == 0 && NV >= 8) {
@@ -285,9 +285,11 @@ __global__ void k_moments(const T* __restrict__ src, float* __restrict__ rho,
     }
 }
 
+// Nodes 0 .. n-1 of a state whose planes are `plane` elements apart (plane = n for a whole
+// lattice; larger for the interior layers of a slab).
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* __restrict__ src,
-                                                                      int64_t n,
+                                                                      int64_t n, int64_t plane,
                                                                       double* __restrict__ part) {
     // Node moments are FP32; each thread adds runs of up to 32 of them in FP32 and the
     // runs in FP64 (FP64 adds are scarce on this GPU; a run of 32 loses < 1e-6 relative).
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* _
          i += (int64_t)gridDim.x * blockDim.x) {
         float g[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * n + i]);
+        for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * plane + i]);
         const NodeMoments m = node_moments(g);
         r[0] += m.drho;
         r[1] += m.jx;
@@ -346,16 +348,16 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_final(const double
 // summed over the lattice; sum_j v_j f_eq,j = rho u at every node). rho may be NULL
 // (rho = 1); u holds dim planes of n values.
 __global__ void __launch_bounds__(kReduceThreads) k_mean_flow_partial(
-    const float* __restrict__ rho, const float* __restrict__ u, int64_t n, int dim,
-    double* __restrict__ part) {
+    const float* __restrict__ rho, const float* __restrict__ u, int64_t n, int64_t plane,
+    int dim, double* __restrict__ part) {
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double r = rho ? (double)rho[i] : 1.0;
         v[0] += r;
         v[1] += r * (double)u[i];
-        v[2] += r * (double)u[n + i];
-        if (dim == 3) v[3] += r * (double)u[2 * n + i];
+        v[2] += r * (double)u[plane + i];
+        if (dim == 3) v[3] += r * (double)u[2 * plane + i];
     }
     block_sum4<kReduceThreads>(v, part + 4 * (int64_t)blockIdx.x);
 }
@@ -574,30 +576,30 @@ int conserved_blocks(int64_t n) {
     return (int)(b < 1 ? 1 : (b > kReduceMaxBlocks ? kReduceMaxBlocks : b));
 }
 
-cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int dim,
-                             double* partials, int nblk, double* out, cudaStream_t st) {
-    k_mean_flow_partial<<<nblk, kReduceThreads, 0, st>>>(rho, u, n, dim, partials);
+cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int64_t plane,
+                             int dim, double* partials, int nblk, double* out, cudaStream_t st) {
+    k_mean_flow_partial<<<nblk, kReduceThreads, 0, st>>>(rho, u, n, plane, dim, partials);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_conserved_final<<<1, kReduceThreads, 0, st>>>(partials, nblk, 0.0, 0.0, 0.0, 1.0, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho_ref,
-                             double jx_ref, double jy_ref, double lambda, double* partials,
-                             int nblk, double* out, cudaStream_t st) {
+cudaError_t launch_conserved(int storage, const void* src, int64_t n, int64_t plane,
+                             double rho_ref, double jx_ref, double jy_ref, double lambda,
+                             double* partials, int nblk, double* out, cudaStream_t st) {
     switch (storage) {
         case kStoreF32:
             k_conserved_partial<float><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const float*>(src), n, partials);
+                static_cast<const float*>(src), n, plane, partials);
             break;
         case kStoreF16:
             k_conserved_partial<__half><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __half*>(src), n, partials);
+                static_cast<const __half*>(src), n, plane, partials);
             break;
         case kStoreBF16:
             k_conserved_partial<__nv_bfloat16><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __nv_bfloat16*>(src), n, partials);
+                static_cast<const __nv_bfloat16*>(src), n, plane, partials);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -596,7 +596,7 @@ __global__ void k_moments3(const T* __restrict__ src, float* __restrict__ rho,
 // FP64 sums of (sum g, sum c g (3), non-finite nodes), 8 doubles per block (5 used).
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_conserved3_partial(const T* __restrict__ src,
-                                                                       int64_t n,
+                                                                       int64_t n, int64_t plane,
                                                                        double* __restrict__ part) {
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     float r[4] = {0.f, 0.f, 0.f, 0.f};
@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved3_partial(const T* 
          i += (int64_t)gridDim.x * blockDim.x) {
         float g[19];
 #pragma unroll
-        for (int j = 0; j < 19; ++j) g[j] = to_f(src[j * n + i]);
+        for (int j = 0; j < 19; ++j) g[j] = to_f(src[j * plane + i]);
         const NodeMoments3 m = node_moments3(g);
         r[0] += m.drho;
         r[1] += m.jx;
@@ -913,21 +913,21 @@ cudaError_t launch_moments3(int storage, const void* src, float* rho, float* u, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_conserved3(int storage, const void* src, int64_t n, const StoreRef3& ref,
-                              double lambda, double* partials, int nblk, double* out,
-                              cudaStream_t st) {
+cudaError_t launch_conserved3(int storage, const void* src, int64_t n, int64_t plane,
+                              const StoreRef3& ref, double lambda, double* partials, int nblk,
+                              double* out, cudaStream_t st) {
     switch (storage) {
         case kStoreF32:
-            k_conserved3_partial<float><<<nblk, kReduceThreads, 0, st>>>(static_cast<const float*>(src), n,
-                                                                         partials);
+            k_conserved3_partial<float><<<nblk, kReduceThreads, 0, st>>>(
+                static_cast<const float*>(src), n, plane, partials);
             break;
         case kStoreF16:
-            k_conserved3_partial<__half><<<nblk, kReduceThreads, 0, st>>>(static_cast<const __half*>(src), n,
-                                                                          partials);
+            k_conserved3_partial<__half><<<nblk, kReduceThreads, 0, st>>>(
+                static_cast<const __half*>(src), n, plane, partials);
             break;
         case kStoreBF16:
             k_conserved3_partial<__nv_bfloat16><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __nv_bfloat16*>(src), n, partials);
+                static_cast<const __nv_bfloat16*>(src), n, plane, partials);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -25,6 +25,11 @@ struct lbmrv_s {
     double lambda = 1.0, rho_ref = 0.0;
     double u_ref[3] = {0.0, 0.0, 0.0};  // reference velocity of the stored deviations
     bool ref_auto = true;  // u_ref := mean flow of the fields of each init_equilibrium
+    // Slab of a larger periodic lattice (lbmrv_set_slab): layers (D2Q9 rows, D3Q19 z-planes)
+    // 1 .. m-2 are the global layers slab_first .. slab_first + m - 3 of slab_extent; layers
+    // 0 and m-1 are halo copies of the neighbouring slabs' edge layers.
+    bool slab = false;
+    int64_t slab_first = 0, slab_extent = 0;
     double s[19] = {0};
     cudaStream_t stream = nullptr;
     void* f[2] = {nullptr, nullptr};
@@ -65,6 +70,17 @@ inline int64_t elem_size(int storage) {
 
 inline size_t state_bytes(const lbmrv_s* h) {
     return (size_t)(h->q * h->n * elem_size(h->storage));
+}
+
+// Nodes of one layer (the unit a slab is cut into) and the number of layers.
+inline int64_t layer_size(const lbmrv_s* h) { return h->dim == 2 ? h->nx : h->nx * h->ny; }
+inline int64_t layer_count(const lbmrv_s* h) { return h->dim == 2 ? h->ny : h->nz; }
+
+// The nodes the handle owns: the whole lattice, or a slab's interior layers (first node and
+// count; the state's planes stay h->n elements apart).
+inline int64_t owned_first(const lbmrv_s* h) { return h->slab ? layer_size(h) : 0; }
+inline int64_t owned_count(const lbmrv_s* h) {
+    return h->slab ? h->n - 2 * layer_size(h) : h->n;
 }
 
 // Make the handle's device current for the duration of a call.
@@ -153,7 +169,9 @@ inline StepArgs make_args(const lbmrv_s* h, int64_t t) {
     a.ref = store_ref(h);
     a.amp_t = (float)(h->amp * time_factor(h, t) / h->lambda);
     a.two_over_nx = (float)(2.0 / (double)h->nx);
-    a.two_over_ny = (float)(2.0 / (double)h->ny);
+    // a slab evaluates the analytic field at the global row: y + y_off of slab_extent rows
+    a.two_over_ny = (float)(2.0 / (double)(h->slab ? h->slab_extent : h->ny));
+    a.y_off = h->slab ? (int)(h->slab_first - 1) : 0;
     a.ut0 = h->ut0;
     a.sin_x = h->sin_x;
     return a;

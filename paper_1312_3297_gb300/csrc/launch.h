@@ -48,16 +48,17 @@ cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, i
 
 int conserved_blocks(int64_t n);
 
+// Sums over nodes 0 .. n-1 of src, whose planes are `plane` >= n elements apart.
 // partials: 4 * nblk doubles of scratch; out: 4 doubles (device). rho_ref, jx_ref, jy_ref:
 // the stored reference state (jx_ref = rho_ref U_x / lambda).
-cudaError_t launch_conserved(int storage, const void* src, int64_t n, double rho_ref,
-                             double jx_ref, double jy_ref, double lambda, double* partials,
-                             int nblk, double* out, cudaStream_t st);
-
-// Sums {rho, rho u_x, rho u_y, rho u_z} of initial fields (rho NULL: 1; u: dim planes of n
-// floats) into out[4] (device); partials: 4 * nblk doubles of scratch.
-cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int dim,
+cudaError_t launch_conserved(int storage, const void* src, int64_t n, int64_t plane,
+                             double rho_ref, double jx_ref, double jy_ref, double lambda,
                              double* partials, int nblk, double* out, cudaStream_t st);
+
+// Sums {rho, rho u_x, rho u_y, rho u_z} over nodes 0 .. n-1 of initial fields (rho NULL:
+// 1; u: dim planes `plane` floats apart) into out[4] (device); partials: 4 * nblk doubles.
+cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int64_t plane,
+                             int dim, double* partials, int nblk, double* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- D3Q19
 int step3_vector_width(int storage, int nx);
@@ -75,10 +76,11 @@ int64_t step3_sum_scratch(int storage, int nv, const StepArgs3& a);
 cudaError_t launch_step3_conserved(int storage, int um, int nv, const void* src, void* dst,
                                    const StepArgs3& a, cudaStream_t st, double lambda,
                                    double* partials, int64_t scratch, double* out);
-// partials: 8 * nblk doubles; out: 5 doubles (sum rho, sum q (3), non-finite nodes).
-cudaError_t launch_conserved3(int storage, const void* src, int64_t n, const StoreRef3& ref,
-                              double lambda, double* partials, int nblk, double* out,
-                              cudaStream_t st);
+// partials: 8 * nblk doubles; out: 5 doubles (sum rho, sum q (3), non-finite nodes) over
+// nodes 0 .. n-1 of src, whose planes are `plane` >= n elements apart.
+cudaError_t launch_conserved3(int storage, const void* src, int64_t n, int64_t plane,
+                              const StoreRef3& ref, double lambda, double* partials, int nblk,
+                              double* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- adjoint (FP32 state)
 struct AdjointArgs {

@@ -48,6 +48,7 @@ int check_common(lbmrv_t h, int64_t n, int64_t seg, const void* ws, size_t ws_by
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "%s: NULL handle", who);
     if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
         return fail(h, LBMRV_E_UNSUPPORTED, "%s: the adjoint needs a D2Q9 FP32 handle", who);
+    if (h->slab) return fail(h, LBMRV_E_UNSUPPORTED, "%s: no adjoint for a slab", who);
     if (n < 1 || seg < 1 || seg > n)
         return fail(h, LBMRV_E_INVAL, "%s: need n >= 1 and 1 <= seg <= n", who);
     if (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign)
@@ -187,8 +188,9 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
 
 int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
     if (!h || !ke_host) return fail(h, LBMRV_E_INVAL, "lbmrv_kinetic_energy: NULL argument");
-    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
-        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_kinetic_energy: needs a D2Q9 FP32 handle");
+    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9 || h->slab)
+        return fail(h, LBMRV_E_UNSUPPORTED,
+                    "lbmrv_kinetic_energy: needs a D2Q9 FP32 handle that is not a slab");
     DeviceGuard g(h->device);
     double* res = h->red + 8 * (size_t)h->red_blocks;
     cudaError_t e = launch_kinetic_energy(static_cast<const float*>(h->f[h->cur]), dL_dS_dev, h->n,

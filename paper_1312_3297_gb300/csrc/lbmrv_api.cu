@@ -60,9 +60,13 @@ void warn_rates(lbmrv_t h, int lattice, const double* s, const char* who) {
 // U_ref stays the mean flow of the whole run. Synchronises the handle's stream.
 int apply_auto_reference(lbmrv_t h, const float* rho, const float* u, const char* who) {
     if (!h->ref_auto) return LBMRV_OK;
+    if (h->slab)
+        return fail(h, LBMRV_E_INVAL,
+                    "%s: a slab needs the reference shared by all slabs (lbmrv_set_reference)",
+                    who);
     double* res = h->red + 8 * (size_t)h->red_blocks;
     double sums[4] = {0.0, 0.0, 0.0, 0.0};
-    cudaError_t e = launch_mean_flow(rho, u, h->n, h->dim, h->red, h->red_blocks, res,
+    cudaError_t e = launch_mean_flow(rho, u, h->n, h->n, h->dim, h->red, h->red_blocks, res,
                                      h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(sums, res, sizeof(sums), cudaMemcpyDeviceToHost, h->stream);
@@ -407,9 +411,13 @@ int lbmrv_conserved3(lbmrv_t h, double out_host[5]) {
     double* res = h->red + 8 * (size_t)h->red_blocks;
     cudaError_t e;
     double tmp[5] = {0, 0, 0, 0, 0};
+    // a slab sums its interior layers only
+    const void* src = static_cast<const char*>(h->f[h->cur]) +
+                      owned_first(h) * elem_size(h->storage);
+    const int64_t count = owned_count(h);
     if (h->dim == 2) {
         double four[4] = {0, 0, 0, 0};
-        e = launch_conserved(h->storage, h->f[h->cur], h->n, h->rho_ref,
+        e = launch_conserved(h->storage, src, count, h->n, h->rho_ref,
                              h->rho_ref * h->u_ref[0] / h->lambda,
                              h->rho_ref * h->u_ref[1] / h->lambda, h->lambda, h->red,
                              h->red_blocks, res, h->stream);
@@ -421,7 +429,7 @@ int lbmrv_conserved3(lbmrv_t h, double out_host[5]) {
         tmp[2] = four[2];
         tmp[4] = four[3];
     } else {
-        e = launch_conserved3(h->storage, h->f[h->cur], h->n, store_ref3(h), h->lambda, h->red,
+        e = launch_conserved3(h->storage, src, count, h->n, store_ref3(h), h->lambda, h->red,
                               h->red_blocks, res, h->stream);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(tmp, res, sizeof(tmp), cudaMemcpyDeviceToHost, h->stream);
@@ -443,8 +451,9 @@ int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]) {
     if (rc != LBMRV_OK) return rc;
     DeviceGuard g(h->device);
     const int nv = choose_width(h, h->f[0], h->f[1]);
-    const bool fused = h->dim == 2 ? nv >= 2
-                                   : step3_fuses_sums(h->storage, nv, (int)h->ny, (int)h->nz);
+    const bool fused = !h->slab && (h->dim == 2 ? nv >= 2
+                                                : step3_fuses_sums(h->storage, nv, (int)h->ny,
+                                                                   (int)h->nz));
     if (!fused) {  // no fused form for this kernel: the step, then the sums' own pass
         rc = lbmrv_step(h, 1);
         return rc != LBMRV_OK ? rc : lbmrv_conserved3(h, out_host);

@@ -121,7 +121,7 @@ extern "C" int lbmrv_conserved_noalloc(const void* state_dev, int storage, const
     if (scratch_for_current_device(&partials) != cudaSuccess) return LBMRV_E_CUDA;
     const int nblk = conserved_blocks(n);  // never more than kReduceMaxBlocks
     if (4 * nblk > kSlots) return LBMRV_E_INVAL;
-    const cudaError_t e = launch_conserved(storage, state_dev, n, rho_ref, 0.0, 0.0, lambda,
+    const cudaError_t e = launch_conserved(storage, state_dev, n, n, rho_ref, 0.0, 0.0, lambda,
                                            partials, nblk, out_dev,
                                            static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? LBMRV_OK : LBMRV_E_CUDA;
