@@ -340,6 +340,7 @@ def gpu_arm(args):
             extras["cascaded_geier_fluid"] = cascaded_measure(torch, inp, fields, k, peak)
             extras["conserved_sums_4096"] = sums_measure(torch, D2Q9, inp, fields)
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
+            extras["adjoint_4096"] = adjoint_step_measure(torch, D2Q9, inp, peak, 4096, 60)
             extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
         out = {
@@ -523,6 +524,42 @@ def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
             "gradient_over_forward_run": round(e0.elapsed_time(e3) / (fwd_ms * n_steps), 3),
             "workspace_gb": round(ws_gb, 2), "loss": ke, "dL_dsnu": ds[4] + ds[5],
             "dL_dA": da, "every_state_stored": all_states}
+
+
+def adjoint_step_measure(torch, D2Q9, inp, peak, size: int, window: int):
+    """The adjoint step alone at size^2 (every state of a `window`-step run checkpointed, so
+    the sweep has no recompute), beside the forward step on the same lattice: ms per step,
+    algorithmic GB/s (108 B/node: S_{k-1} and mu_{k+1} read, mu_k written) and its fraction
+    of the measured copy bandwidth."""
+    n = size * size
+    d = inp.noisy_shear_wave(size, size, seed=0)
+    sim = D2Q9(size, size, S_RATES, mode="prescribed")
+    sim.set_utilde(None, UT_AMP, UT_PERIOD)
+    rho = torch.as_tensor(d["rho"], dtype=torch.float32, device="cuda")
+    u = torch.stack([torch.as_tensor(d[k], dtype=torch.float32, device="cuda")
+                     for k in ("ux", "uy")])
+    st = sim.stream
+    sim.init_equilibrium(rho, u[0], u[1])
+    sim.step(5)
+    fwd_ms = time_steps(sim, window, torch) / window
+    ws = sim.adjoint_workspace(window, 1)
+    sim.init_equilibrium(rho, u[0], u[1])
+    sim.forward_checkpointed(window, 1, ws)
+    _, dlds = sim.kinetic_energy(grad=True)
+    sim.adjoint(window, 1, ws, dlds)  # warm
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    sim.adjoint(window, 1, ws, dlds)
+    b.record(st)
+    b.synchronize()
+    adj_ms = a.elapsed_time(b) / window
+    del ws
+    sim.close()
+    torch.cuda.empty_cache()
+    gbs = 108 * n / (adj_ms * 1e-3) / 1e9
+    return {"forward_ms_per_step": round(fwd_ms, 5), "adjoint_ms_per_step": round(adj_ms, 5),
+            "adjoint_over_forward": round(adj_ms / fwd_ms, 3), "adjoint_gbs": round(gbs, 1),
+            "adjoint_frac": round(gbs / peak, 4)}
 
 
 def adjoint_arm(args):
