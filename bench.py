@@ -341,6 +341,9 @@ def gpu_arm(args):
             extras["conserved_sums_4096"] = sums_measure(torch, D2Q9, inp, fields)
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
             extras["adjoint_4096"] = adjoint_step_measure(torch, D2Q9, inp, peak, 4096, 60)
+            extras["adjoint_16bit_1024"] = {
+                st: adjoint_step_measure(torch, D2Q9, inp, peak, 1024, 1000, st)
+                for st in ("fp16", "bf16")}
             extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
         out = {
@@ -526,14 +529,15 @@ def adjoint_measure(torch, D2Q9, inp, peak, n_steps: int = 2000):
             "dL_dA": da, "every_state_stored": all_states}
 
 
-def adjoint_step_measure(torch, D2Q9, inp, peak, size: int, window: int):
+def adjoint_step_measure(torch, D2Q9, inp, peak, size: int, window: int, storage="fp32"):
     """The adjoint step alone at size^2 (every state of a `window`-step run checkpointed, so
-    the sweep has no recompute), beside the forward step on the same lattice: ms per step,
-    algorithmic GB/s (108 B/node: S_{k-1} and mu_{k+1} read, mu_k written) and its fraction
-    of the measured copy bandwidth."""
+    the sweep has no recompute), beside the forward step on the same lattice and storage:
+    ms per step, algorithmic GB/s (S_{k-1} read in the storage type, mu_{k+1} read and mu_k
+    written in FP32: 108 B/node, 90 B/node with 16-bit states) and its fraction of the
+    measured copy bandwidth."""
     n = size * size
     d = inp.noisy_shear_wave(size, size, seed=0)
-    sim = D2Q9(size, size, S_RATES, mode="prescribed")
+    sim = D2Q9(size, size, S_RATES, mode="prescribed", storage=storage)
     sim.set_utilde(None, UT_AMP, UT_PERIOD)
     rho = torch.as_tensor(d["rho"], dtype=torch.float32, device="cuda")
     u = torch.stack([torch.as_tensor(d[k], dtype=torch.float32, device="cuda")
@@ -556,8 +560,9 @@ def adjoint_step_measure(torch, D2Q9, inp, peak, size: int, window: int):
     del ws
     sim.close()
     torch.cuda.empty_cache()
-    gbs = 108 * n / (adj_ms * 1e-3) / 1e9
-    return {"forward_ms_per_step": round(fwd_ms, 5), "adjoint_ms_per_step": round(adj_ms, 5),
+    gbs = (BYTES_PER_NODE[storage] // 2 + 72) * n / (adj_ms * 1e-3) / 1e9
+    return {"storage": storage,
+            "forward_ms_per_step": round(fwd_ms, 5), "adjoint_ms_per_step": round(adj_ms, 5),
             "adjoint_over_forward": round(adj_ms / fwd_ms, 3), "adjoint_gbs": round(gbs, 1),
             "adjoint_frac": round(gbs / peak, 4)}
 

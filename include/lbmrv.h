@@ -267,15 +267,19 @@ LBMRV_API int lbmrv_set_rates(lbmrv_t h, const double* s);
  * where P^T is a push (the transpose of the pull). J_C^T is the hand-derived transpose of
  * the shifted relaxation (moments, equilibrium moments, T(u~), S, T(-u~), M(0)^{-1}),
  * including the dependence of u~ = q/rho on the populations. Parameter gradients are
- * summed over nodes and steps in FP64. D2Q9 with FP32 storage only (else
- * LBMRV_E_UNSUPPORTED).
+ * summed over nodes and steps in FP64. D2Q9 only (else LBMRV_E_UNSUPPORTED), with any
+ * storage type: with FP16 / BF16 storage the checkpoints and recomputed states are the
+ * handle's 16-bit states, the adjoint vectors stay FP32, and J_C is the derivative of the
+ * FP32 relaxation at the stored states (the rounding to the storage type is taken as the
+ * identity). Not for slabs.
  * Memory: sqrt(N)-style checkpointing. lbmrv_forward_checkpointed stores every seg-th
  * state; lbmrv_adjoint recomputes each segment from its checkpoint (one extra forward in
  * total) and walks it backwards. */
 
 /* Bytes of the caller-owned workspace for n steps with checkpoints every seg steps
- * (1 <= seg <= n): ceil(n/seg) + seg + 1 states of 36 bytes per node, plus
- * accumulators. -1 on invalid arguments. */
+ * (1 <= seg <= n): ceil(n/seg) + seg - 1 states in the storage type (9 values per node),
+ * two FP32 adjoint states (36 bytes per node each), plus accumulators. -1 on invalid
+ * arguments. */
 LBMRV_API int64_t lbmrv_adjoint_workspace_bytes(lbmrv_t h, int64_t n, int64_t seg);
 
 /* Advance n steps from the current state (time t0) like lbmrv_step, storing the states
@@ -302,7 +306,8 @@ LBMRV_API int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, siz
                             double* dL_damp_host, float* dL_dut0_dev);
 
 /* Kinetic energy L = 1/2 sum_x |q|^2 / rho of the current state (FP64 sum, synchronous)
- * and, when dL_dS_dev (device FP32 [9][nx*ny]) is not NULL, its gradient dL/dS. */
+ * and, when dL_dS_dev (device FP32 [9][nx*ny]) is not NULL, its gradient dL/dS (with
+ * respect to the stored values, in FP32 whatever the storage type). */
 LBMRV_API int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev);
 
 /* Adjoint of lbmrv_moments at the current state: dL/dS from dL/drho (device FP32 [nx*ny]

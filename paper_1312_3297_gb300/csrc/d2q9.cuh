@@ -121,6 +121,11 @@ __device__ __forceinline__ F2 recip(F2 x) {
     unpack2(x, a, b);
     return pack2(recip<RCP>(a), recip<RCP>(b));
 }
+
+template <int RCP = RCP_RN>
+__device__ __forceinline__ F1 recip(F1 x) {
+    return F1(recip<RCP>(x.v));
+}
 #endif
 
 // The relaxation of Section 1.2 in the shifted form of Section 1.3, in place on the

@@ -14,11 +14,12 @@
 
 namespace lbmrv {
 
-// The reverse relaxation of one node (R = float) or of two nodes at once (R = F2, one node
-// per lane, packed FP32 instructions; each lane rounds exactly as the float instance, since
-// every fused multiply-add is written out). UM = UM_FLUID takes u = q / rho of the node
-// (ux, uy are ignored) and folds dL/du into the moments' adjoint; UM = UM_ZERO is the
-// fixed-frame scheme. RCP: the form of 1/rho (see recip).
+// The reverse relaxation of one node (R = F1, scalar FP32 whose arithmetic the compiler does
+// not contract) or of two nodes at once (R = F2, one node per lane, packed FP32
+// instructions). Every fused multiply-add is written out.
+// UM = UM_FLUID takes u = q / rho of the node (ux, uy are ignored) and folds dL/du into the
+// moments' adjoint; UM = UM_ZERO is the fixed-frame scheme. RCP: the form of 1/rho (see
+// recip).
 //   g      the pre-relaxation deviations (as pulled by the forward step)
 //   a      dL/dg*, the adjoint of the relaxed deviations
 //   out    dL/dg = a^T dg*/dg

@@ -51,4 +51,18 @@ __device__ __forceinline__ F2 fma_(F2 a, F2 b, F2 c) {
     return r;
 }
 
+// One FP32 value whose arithmetic the compiler never contracts into fused multiply-adds
+// (each operator is a single .rn operation): the scalar counterpart of F2 for code written
+// once for both.
+struct F1 {
+    float v;
+    __device__ __forceinline__ F1() {}
+    __device__ __forceinline__ F1(float a) : v(a) {}
+};
+
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1(__fadd_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1(__fsub_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1(__fmul_rn(a.v, b.v)); }
+__device__ __forceinline__ F1 fma_(F1 a, F1 b, F1 c) { return F1(__fmaf_rn(a.v, b.v, c.v)); }
+
 }  // namespace lbmrv

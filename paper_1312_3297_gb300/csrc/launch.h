@@ -82,7 +82,8 @@ cudaError_t launch_conserved3(int storage, const void* src, int64_t n, int64_t p
                               const StoreRef3& ref, double lambda, double* partials, int nblk,
                               double* out, cudaStream_t st);
 
-// ---------------------------------------------------------------- adjoint (FP32 state)
+// ---------------------------------------------------------------- adjoint (FP32 adjoint
+// vectors; forward states in the handle's storage type)
 struct AdjointArgs {
     StepArgs step;     // step arguments of the relaxation being reversed (time k)
     float da_factor;   // d(u~/lambda)/dA = cos(2 pi k / P) / lambda for dL/dA
@@ -94,19 +95,24 @@ dim3 adjoint_grid(int nx, int ny, int nv);
 int64_t adjoint_blocks(int nx, int ny, int nv);
 
 // mu_out = J_C(P s_prev)^T a, a = (gather ? P^T a_in : a_in); accumulates into aa.acc;
-// nv nodes per thread (1, 2 or 4, dividing nx unless 1).
-cudaError_t launch_adjoint_step(int um, int nv, const float* s_prev, const float* a_in,
-                                bool gather, float* mu_out, const AdjointArgs& aa,
-                                cudaStream_t st);
+// nv nodes per thread (1, 2 or 4, dividing nx unless 1); s_prev in the storage type.
+cudaError_t launch_adjoint_step(int storage, int um, int nv, const void* s_prev,
+                                const float* a_in, bool gather, float* mu_out,
+                                const AdjointArgs& aa, cudaStream_t st);
+// The same for FP16 / BF16 forward states (d2q9_adjoint16.cu).
+cudaError_t launch_adjoint_step16(int storage, int um, int nv, const void* s_prev,
+                                  const float* a_in, bool gather, float* mu_out,
+                                  const AdjointArgs& aa, cudaStream_t st);
 cudaError_t launch_gather(const float* src, float* dst, int nx, int ny, cudaStream_t st);
 cudaError_t launch_acc_final(const double* acc, int64_t nblk, double* out, cudaStream_t st);
 cudaError_t launch_equilibrium_vjp(const float* rho, const float* u, const float* a, float* drho,
                                    float* du, int64_t n, float inv_lambda, cudaStream_t st);
-cudaError_t launch_moments_vjp(const float* g, const float* drho, const float* du, float* out,
-                               int64_t n, const StoreRef& ref, float lambda, cudaStream_t st);
+cudaError_t launch_moments_vjp(int storage, const void* g, const float* drho, const float* du,
+                               float* out, int64_t n, const StoreRef& ref, float lambda,
+                               cudaStream_t st);
 // partials: 4 * nblk doubles of scratch (slot 0 of each used); out: 1 double (device).
-cudaError_t launch_kinetic_energy(const float* g, float* grad, int64_t n, const StoreRef& ref,
-                                  float lambda, double* partials, int nblk, double* out,
-                                  cudaStream_t st);
+cudaError_t launch_kinetic_energy(int storage, const void* g, float* grad, int64_t n,
+                                  const StoreRef& ref, float lambda, double* partials, int nblk,
+                                  double* out, cudaStream_t st);
 
 }  // namespace lbmrv

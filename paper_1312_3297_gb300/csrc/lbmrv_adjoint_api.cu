@@ -15,12 +15,12 @@ constexpr size_t kAlign = 256;
 
 size_t round_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-// Workspace: C checkpoints S_{t0 + c seg} (c = 0 .. C-1), seg - 1 recomputed states of the
-// current segment, two adjoint states, then 8 FP64 accumulators per adjoint block and 8
-// results.
+// Workspace: C checkpoints S_{t0 + c seg} (c = 0 .. C-1) and seg - 1 recomputed states of the
+// current segment, in the handle's storage type; two FP32 adjoint states; then 8 FP64
+// accumulators per adjoint block and 8 results.
 struct WsLayout {
     int64_t C = 0, seg = 0, nblk = 0;
-    size_t state = 0, off_seg = 0, off_mu = 0, off_acc = 0, total = 0;
+    size_t state = 0, mu = 0, off_seg = 0, off_mu = 0, off_acc = 0, total = 0;
 };
 
 // Nodes per thread of the adjoint kernel: the handle's kernel width when it is 1, 2 or 4,
@@ -34,11 +34,12 @@ WsLayout layout(const lbmrv_s* h, int64_t n, int64_t seg) {
     WsLayout L;
     L.seg = seg;
     L.C = (n + seg - 1) / seg;
-    L.state = round_up((size_t)(9 * h->n) * sizeof(float));
+    L.state = round_up(state_bytes(h));
+    L.mu = round_up((size_t)(9 * h->n) * sizeof(float));
     L.nblk = adjoint_blocks((int)h->nx, (int)h->ny, adjoint_nv(h));
     L.off_seg = (size_t)L.C * L.state;
     L.off_mu = L.off_seg + (size_t)(seg - 1) * L.state;
-    L.off_acc = L.off_mu + 2 * L.state;
+    L.off_acc = L.off_mu + 2 * L.mu;
     L.total = L.off_acc + round_up((size_t)(L.nblk + 1) * 8 * sizeof(double));
     return L;
 }
@@ -46,8 +47,8 @@ WsLayout layout(const lbmrv_s* h, int64_t n, int64_t seg) {
 int check_common(lbmrv_t h, int64_t n, int64_t seg, const void* ws, size_t ws_bytes,
                  const char* who, WsLayout* out) {
     if (!h) return fail(nullptr, LBMRV_E_INVAL, "%s: NULL handle", who);
-    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
-        return fail(h, LBMRV_E_UNSUPPORTED, "%s: the adjoint needs a D2Q9 FP32 handle", who);
+    if (h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "%s: the adjoint needs a D2Q9 handle", who);
     if (h->slab) return fail(h, LBMRV_E_UNSUPPORTED, "%s: no adjoint for a slab", who);
     if (n < 1 || seg < 1 || seg > n)
         return fail(h, LBMRV_E_INVAL, "%s: need n >= 1 and 1 <= seg <= n", who);
@@ -79,7 +80,7 @@ int lbmrv_forward_checkpointed(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev,
     int rc = check_common(h, n, seg, ws_dev, ws_bytes, "lbmrv_forward_checkpointed", &L);
     if (rc != LBMRV_OK) return rc;
     DeviceGuard g(h->device);
-    const size_t bytes = (size_t)(9 * h->n) * sizeof(float);
+    const size_t bytes = state_bytes(h);
     // the pack width must suit both the handle's buffers and the checkpoint slots
     const int nv_f = choose_width(h, h->f[0], h->f[1]), nv_w = choose_width(h, ws_dev, ws_dev);
     const int nv = nv_f < nv_w ? nv_f : nv_w;
@@ -139,7 +140,7 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
     double* acc = reinterpret_cast<double*>(at(ws_dev, L.off_acc));
     double* res = acc + 8 * L.nblk;
     float* mu[2] = {reinterpret_cast<float*>(at(ws_dev, L.off_mu)),
-                    reinterpret_cast<float*>(at(ws_dev, L.off_mu + L.state))};
+                    reinterpret_cast<float*>(at(ws_dev, L.off_mu + L.mu))};
     cudaError_t e = cudaMemsetAsync(acc, 0, (size_t)L.nblk * 8 * sizeof(double), h->stream);
     if (e == cudaSuccess && dL_dut0_dev)
         e = cudaMemsetAsync(dL_dut0_dev, 0, (size_t)(2 * h->n) * sizeof(float), h->stream);
@@ -149,23 +150,25 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
     for (int64_t c = L.C - 1; c >= 0 && e == cudaSuccess; --c) {
         const int64_t base = c * seg;
         const int64_t khi = base + seg < n ? base + seg : n;
-        const float* ck = reinterpret_cast<const float*>(at(ws_dev, (size_t)c * L.state));
+        const void* ck = at(ws_dev, (size_t)c * L.state);
         auto seg_state = [&](int64_t k) {  // S_k for base < k < khi
-            return reinterpret_cast<float*>(at(ws_dev, L.off_seg + (size_t)(k - base - 1) * L.state));
+            return static_cast<void*>(at(ws_dev, L.off_seg + (size_t)(k - base - 1) * L.state));
         };
-        const float* src = ck;
+        const void* src = ck;
         for (int64_t k = base + 1; k < khi && e == cudaSuccess; ++k) {
-            e = launch_step(LBMRV_FP32, um, nv, src, seg_state(k), make_args(h, t0 + k), h->stream);
+            e = launch_step(h->storage, um, nv, src, seg_state(k), make_args(h, t0 + k),
+                            h->stream);
             src = seg_state(k);
         }
         for (int64_t k = khi; k > base && e == cudaSuccess; --k) {
-            const float* s_prev = (k - 1 == base) ? ck : seg_state(k - 1);
+            const void* s_prev = (k - 1 == base) ? ck : seg_state(k - 1);
             AdjointArgs aa;
             aa.step = make_args(h, t0 + k);
             aa.da_factor = (float)(time_factor(h, t0 + k) / h->lambda);
             aa.dut0 = dL_dut0_dev;
             aa.acc = acc;
-            e = launch_adjoint_step(um, anv, s_prev, a, gather, mu[pp], aa, h->stream);
+            e = launch_adjoint_step(h->storage, um, anv, s_prev, a, gather, mu[pp], aa,
+                                    h->stream);
             a = mu[pp];
             gather = true;
             pp ^= 1;
@@ -188,12 +191,12 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
 
 int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
     if (!h || !ke_host) return fail(h, LBMRV_E_INVAL, "lbmrv_kinetic_energy: NULL argument");
-    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9 || h->slab)
+    if (h->lattice != LBMRV_D2Q9 || h->slab)
         return fail(h, LBMRV_E_UNSUPPORTED,
-                    "lbmrv_kinetic_energy: needs a D2Q9 FP32 handle that is not a slab");
+                    "lbmrv_kinetic_energy: needs a D2Q9 handle that is not a slab");
     DeviceGuard g(h->device);
     double* res = h->red + 8 * (size_t)h->red_blocks;
-    cudaError_t e = launch_kinetic_energy(static_cast<const float*>(h->f[h->cur]), dL_dS_dev, h->n,
+    cudaError_t e = launch_kinetic_energy(h->storage, h->f[h->cur], dL_dS_dev, h->n,
                                           store_ref(h), (float)h->lambda, h->red,
                                           h->red_blocks, res, h->stream);
     if (e == cudaSuccess)
@@ -206,10 +209,10 @@ int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
 int lbmrv_moments_vjp(lbmrv_t h, const float* dL_drho_dev, const float* dL_du_dev,
                       float* dL_dS_dev) {
     if (!h || !dL_dS_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_moments_vjp: NULL argument");
-    if (h->storage != LBMRV_FP32 || h->lattice != LBMRV_D2Q9)
-        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_moments_vjp: needs a D2Q9 FP32 handle");
+    if (h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_moments_vjp: needs a D2Q9 handle");
     DeviceGuard g(h->device);
-    cudaError_t e = launch_moments_vjp(static_cast<const float*>(h->f[h->cur]), dL_drho_dev,
+    cudaError_t e = launch_moments_vjp(h->storage, h->f[h->cur], dL_drho_dev,
                                        dL_du_dev, dL_dS_dev, h->n, store_ref(h),
                                        (float)h->lambda, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_moments_vjp");

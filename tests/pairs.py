@@ -101,7 +101,7 @@ def oracle_kinetic_energy(rho0, u0, s, mode, steps, amp=0.0, period=0.0, ut0=Non
 
 
 def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=None,
-                  field_grad=False, u_ref=None):
+                  field_grad=False, u_ref=None, storage="fp32", width=0):
     """Kinetic energy after `steps` steps and its gradients from the CUDA adjoint:
     (L, dL/du0 [2, ny, nx], dL/ds [9], dL/dA, dL/du~0 or None)."""
     import torch
@@ -109,7 +109,9 @@ def gpu_gradients(nx, ny, s, mode, steps, seg, fields, amp=0.0, period=0.0, ut0=
     from paper_1312_3297_gb300 import D2Q9
 
     rho, ux, uy = fields
-    sim = D2Q9(nx, ny, s, mode=mode, u_ref=u_ref)
+    sim = D2Q9(nx, ny, s, mode=mode, u_ref=u_ref, storage=storage)
+    if width:
+        sim.set_kernel_width(width)
     if MODES[mode] == 2:
         sim.set_utilde(None if ut0 is None else torch.as_tensor(ut0, dtype=torch.float32),
                        amp, period)

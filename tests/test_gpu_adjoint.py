@@ -6,6 +6,9 @@ initial velocity field, the shear rate s_nu and the amplitude A of a prescribed 
 compared with reverse-mode differentiation of the FP64 PyTorch statement of the scheme and
 with central differences (eps = 1e-4) of the FP64 C oracle; the bar is 1e-4 relative error.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -256,3 +259,61 @@ def test_unaligned_gradient_buffers():
     np.testing.assert_array_equal(d_view[0].cpu().numpy(), d_ok[0].cpu().numpy())
     assert d_view[1] == d_ok[1]
     sim.close()
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16"])
+@pytest.mark.parametrize("mode", ["zero", "fluid", "prescribed"])
+def test_adjoint_widths_agree(storage, mode):
+    """The reverse step on 4- and 2-node packs (node pairs by packed FP32 instructions) and on
+    one node per thread (the scalar form of the same arithmetic). With u~ = 0 or q/rho the
+    two packed widths give the same bits of dL/du0 (the forward kernels of those widths
+    store the same bits too); with the prescribed field the forward kernels of different
+    widths may round the field's product differently. Everything else agrees to rounding
+    (1e-6), including the parameter gradients, which are sums taken in a width-dependent
+    order. A row of 72 nodes leaves part of a warp idle at 4-node packs."""
+    nx, ny, steps = 72, 20, 24
+    fields = f32_fields(inp.noisy_shear_wave(nx, ny, seed=8))
+    outs = {w: gpu_gradients(nx, ny, S, mode, steps, 5, fields, 0.03, 40.0, storage=storage,
+                             width=w) for w in (4, 2, 1)}
+    if mode != "prescribed":
+        np.testing.assert_array_equal(outs[2][1], outs[4][1])
+    for w in (2, 1):
+        assert _rel(outs[w][1], outs[4][1]) <= 1e-6
+        np.testing.assert_allclose(outs[w][2], outs[4][2], rtol=1e-6, atol=1e-9)
+        assert abs(outs[w][3] - outs[4][3]) <= 1e-6 * max(abs(outs[4][3]), 1e-12)
+
+
+def _report(name, vals):
+    out = os.environ.get("LBMRV_PRECISION_REPORT")
+    if out:
+        with open(out, "a") as fh:
+            fh.write(json.dumps(dict(case=name, **vals)) + "\n")
+
+
+# Relative gradient errors against FP64 reverse mode measured with 16-bit storage (64^2
+# noisy shear wave, prescribed u~, kinetic-energy loss, 64 steps); each bound is the
+# measured error with a margin, so that a change that makes it worse is caught.
+GRAD16_BOUNDS = {"fp16": dict(du0=3e-3, s_nu=3e-3, amp=3e-3),
+                 "bf16": dict(du0=3e-2, s_nu=3e-2, amp=3e-2)}
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+def test_16bit_storage_gradients_against_fp64_reverse_mode(storage):
+    """The adjoint workload's shape at 64^2 with the states stored in FP16 / BF16 (the
+    checkpoints and the recomputed states are 16-bit; the adjoint vectors FP32): the
+    gradients with respect to u0, s_nu and A against FP64 reverse mode of the FP64
+    statement of the scheme. The errors are those of the 16-bit forward trajectory."""
+    from oracle import torch_ref as tr
+
+    n, steps, seg = 64, 64, 8
+    fields = f32_fields(inp.noisy_shear_wave(n, n, seed=0))
+    rho, ux, uy = fields
+    L, du0, ds, da, _ = gpu_gradients(n, n, S, "prescribed", steps, seg, fields, 0.03, 1000.0,
+                                      storage=storage)
+    Lr, gur, gsr, gar = tr.loss_and_grads(rho, np.stack([ux, uy]), 1.0, S, 1.9, 2, steps,
+                                          tr.analytic_base_field(n, n), 0.03, 1000.0)
+    errs = dict(loss=abs(L - Lr) / abs(Lr), du0=_rel(du0, gur),
+                s_nu=abs(ds[4] + ds[5] - gsr) / abs(gsr), amp=abs(da - gar) / abs(gar))
+    _report(f"adjoint-{storage}-64x64-64", errs)
+    for k, bound in GRAD16_BOUNDS[storage].items():
+        assert errs[k] <= bound, (k, errs)
