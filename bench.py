@@ -293,6 +293,14 @@ def gpu_arm(args):
         clocks.stop()
         clock_info = clocks.summary(first, last)
     ms = max_over_ranks(ms, torch.device("cuda", local))
+    # The K timed steps can be a few milliseconds; repeats of at least 100 ms each, taken
+    # after the timed region, show how stable the per-step time is.
+    repeats = None
+    if rank == 0 and not args.no_extras:
+        k_rep = max(args.steps, int(100.0 / max(ms / args.steps, 1e-3)) + 1)
+        runs = [time_steps(sim, k_rep, torch) / k_rep for _ in range(5)]
+        repeats = {"steps_per_run": k_rep, "ms_per_step_runs": [round(r, 5) for r in runs],
+                   "ms_per_step_median": round(statistics.median(runs), 5)}
     finite = sim.conserved(allow_nonfinite=True)
     sim.close()
     per_step_ms = ms / args.steps
@@ -369,6 +377,9 @@ def gpu_arm(args):
             "cpu_baseline": cpu,
             "modes": extras,
             "wall_ms_timed_region": round(wall_ms, 2),
+            "repeats": repeats,
+            "ms_per_step_x_sm_mhz": (round(per_step_ms * clock_info["sm_mhz"], 2)
+                                     if clocks and clock_info.get("sm_mhz") else None),
             "nonfinite_nodes": finite[3],
         }
     if world > 1:
