@@ -347,6 +347,8 @@ def gpu_arm(args):
             del big
             extras["cascaded_geier_fluid"] = cascaded_measure(torch, inp, fields, k, peak)
             extras["conserved_sums_4096"] = sums_measure(torch, D2Q9, inp, fields)
+            extras["slab_one_rank_4096"] = slab_measure(torch, D2Q9, inp, fields, k, peak,
+                                                        per_step_ms)
             extras["adjoint_1024"] = adjoint_measure(torch, D2Q9, inp, peak)
             extras["adjoint_4096"] = adjoint_step_measure(torch, D2Q9, inp, peak, 4096, 60)
             extras["adjoint_16bit_1024"] = {
@@ -387,6 +389,33 @@ def gpu_arm(args):
         dist.destroy_process_group()
     if out is not None:
         print(json.dumps(out), flush=True)
+
+
+def slab_measure(torch, D2Q9, inp, fields, steps, peak, ref_ms):
+    """The headline workload through the slab driver with one slab (its own neighbour): each
+    step packs the two faces' crossing populations, copies them into the halo buffers,
+    unpacks them into the halo rows and runs the fused step on 4096 + 2 rows; the cost of the
+    decomposition's machinery against the plain step (ref_ms per step)."""
+    from paper_1312_3297_gb300.slab import Slab
+
+    sl = Slab(D2Q9, (L, L), S_RATES, mode="prescribed")
+    sl.sim.set_utilde(None, UT_AMP, UT_PERIOD)
+    sl.init_equilibrium(*(torch.as_tensor(fields[k], dtype=torch.float32)
+                          for k in ("rho", "ux", "uy")))
+    sl.step(3)
+    st = sl.sim.stream
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(st)
+    sl.step(steps)
+    b.record(st)
+    b.synchronize()
+    per = a.elapsed_time(b) / steps
+    sl.close()
+    n = L * L
+    return {"ms_per_step": round(per, 5), "mlups": round(n / (per * 1e-3) / 1e6, 1),
+            "frac": round(72 * n / (per * 1e-3) / 1e9 / peak, 4),
+            "over_plain_step": round(per / ref_ms, 4),
+            "kernels_per_step": "2 pack + 2 halo copies + 2 unpack + 1 step"}
 
 
 def sums_measure(torch, D2Q9, inp, fields, reps: int = 30):
