@@ -21,6 +21,7 @@
 #include "handle.h"
 #include "launch.h"
 #include "lbmrv.h"
+#include "pdl.cuh"
 
 using namespace lbmrv;
 
@@ -81,18 +82,26 @@ Face recv_face(int lattice, int64_t m, int side) {
     return side == 0 ? Face{0, crossing(lattice, +1)} : Face{m - 1, crossing(lattice, -1)};
 }
 
-// Copies between a face buffer and the state, value b <-> state[j_k n + layer L + i].
-// PACK: buffer <- state; otherwise state <- buffer. E: an unsigned type of the storage
-// element's size (the values are moved as bits).
+// Copies between the two face buffers and the state, value b of face f (blockIdx.y) <->
+// state[j_k n + layer L + i]. PACK: buffers <- state; otherwise state <- buffers. E: an
+// unsigned type of the storage element's size (the values are moved as bits). A NULL
+// buffer skips its face. Launched as a dependent launch: it waits for the work before it in
+// the stream (the step that wrote the state, or the copy that filled the buffers) before
+// touching memory.
 template <typename E, bool PACK>
-__global__ void k_halo_copy(E* __restrict__ state, E* __restrict__ buf, int64_t n, int64_t L,
-                            int64_t layer, Crossing pops) {
-    const int64_t total = (int64_t)pops.count * L;
+__global__ void k_halo_copy(E* __restrict__ state, E* __restrict__ buf_lo,
+                            E* __restrict__ buf_hi, int64_t n, int64_t L, Face lo, Face hi) {
+    pdl_wait_prior();
+    pdl_allow_next();
+    const Face& f = blockIdx.y == 0 ? lo : hi;
+    E* __restrict__ buf = blockIdx.y == 0 ? buf_lo : buf_hi;
+    if (!buf) return;
+    const int64_t total = (int64_t)f.pops.count * L;
     for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < total;
          b += (int64_t)gridDim.x * blockDim.x) {
         const int k = (int)(b / L);
         const int64_t i = b - (int64_t)k * L;
-        const int64_t off = (int64_t)pops.j[k] * n + layer * L + i;
+        const int64_t off = (int64_t)f.pops.j[k] * n + f.layer * L + i;
         if (PACK)
             buf[b] = state[off];
         else
@@ -100,19 +109,19 @@ __global__ void k_halo_copy(E* __restrict__ state, E* __restrict__ buf, int64_t 
     }
 }
 
+// Both faces in one launch (grid y = face).
 template <bool PACK>
-cudaError_t halo_copy(const lbmrv_s* h, void* buf, const Face& f) {
-    const int64_t L = layer_size(h), total = (int64_t)f.pops.count * L;
-    const int g = grid_stride_blocks(total, 256);
+cudaError_t halo_copy(const lbmrv_s* h, void* buf_lo, void* buf_hi, const Face& lo,
+                      const Face& hi) {
+    const int64_t L = layer_size(h), total = (int64_t)lo.pops.count * L;
+    const dim3 grid((unsigned)grid_stride_blocks(total, 256), 2);
     if (elem_size(h->storage) == 4)
-        k_halo_copy<uint32_t, PACK><<<g, 256, 0, h->stream>>>(
-            static_cast<uint32_t*>(h->f[h->cur]), static_cast<uint32_t*>(buf), h->n, L,
-            f.layer, f.pops);
-    else
-        k_halo_copy<uint16_t, PACK><<<g, 256, 0, h->stream>>>(
-            static_cast<uint16_t*>(h->f[h->cur]), static_cast<uint16_t*>(buf), h->n, L,
-            f.layer, f.pops);
-    return cudaGetLastError();
+        return launch_pdl(k_halo_copy<uint32_t, PACK>, grid, dim3(256), h->stream,
+                          static_cast<uint32_t*>(h->f[h->cur]), static_cast<uint32_t*>(buf_lo),
+                          static_cast<uint32_t*>(buf_hi), h->n, L, lo, hi);
+    return launch_pdl(k_halo_copy<uint16_t, PACK>, grid, dim3(256), h->stream,
+                      static_cast<uint16_t*>(h->f[h->cur]), static_cast<uint16_t*>(buf_lo),
+                      static_cast<uint16_t*>(buf_hi), h->n, L, lo, hi);
 }
 
 }  // namespace
@@ -170,10 +179,10 @@ int lbmrv_halo_pack(lbmrv_t h, void* send_lo_dev, void* send_hi_dev) {
     if (!h->slab) return fail(h, LBMRV_E_INVAL, "lbmrv_halo_pack: not a slab (lbmrv_set_slab)");
     DeviceGuard g(h->device);
     const int64_t m = layer_count(h);
-    cudaError_t e = cudaSuccess;
-    if (send_lo_dev) e = halo_copy<true>(h, send_lo_dev, send_face(h->lattice, m, 0));
-    if (e == cudaSuccess && send_hi_dev)
-        e = halo_copy<true>(h, send_hi_dev, send_face(h->lattice, m, 1));
+    if (!send_lo_dev && !send_hi_dev) return LBMRV_OK;
+    const cudaError_t e = halo_copy<true>(h, send_lo_dev, send_hi_dev,
+                                          send_face(h->lattice, m, 0),
+                                          send_face(h->lattice, m, 1));
     return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_halo_pack");
 }
 
@@ -183,11 +192,11 @@ int lbmrv_halo_unpack(lbmrv_t h, const void* recv_lo_dev, const void* recv_hi_de
         return fail(h, LBMRV_E_INVAL, "lbmrv_halo_unpack: not a slab (lbmrv_set_slab)");
     DeviceGuard g(h->device);
     const int64_t m = layer_count(h);
-    cudaError_t e = cudaSuccess;
-    if (recv_lo_dev)
-        e = halo_copy<false>(h, const_cast<void*>(recv_lo_dev), recv_face(h->lattice, m, 0));
-    if (e == cudaSuccess && recv_hi_dev)
-        e = halo_copy<false>(h, const_cast<void*>(recv_hi_dev), recv_face(h->lattice, m, 1));
+    if (!recv_lo_dev && !recv_hi_dev) return LBMRV_OK;
+    const cudaError_t e = halo_copy<false>(h, const_cast<void*>(recv_lo_dev),
+                                           const_cast<void*>(recv_hi_dev),
+                                           recv_face(h->lattice, m, 0),
+                                           recv_face(h->lattice, m, 1));
     return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_halo_unpack");
 }
 

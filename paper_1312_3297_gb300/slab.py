@@ -108,9 +108,12 @@ class Slab:
 
     # -- stepping
     def exchange(self):
-        B.lbmrv_halo_pack(self.sim.h, self.send_lo, self.send_hi)
-        exchange_faces(self.send_lo, self.send_hi, self.recv_lo, self.recv_hi, self.rank,
-                       self.world, self.group)
+        if self.world == 1:  # its own neighbour: pack straight into the other face's halo
+            B.lbmrv_halo_pack(self.sim.h, self.recv_hi, self.recv_lo)
+        else:
+            B.lbmrv_halo_pack(self.sim.h, self.send_lo, self.send_hi)
+            exchange_faces(self.send_lo, self.send_hi, self.recv_lo, self.recv_hi, self.rank,
+                           self.world, self.group)
         B.lbmrv_halo_unpack(self.sim.h, self.recv_lo, self.recv_hi)
 
     def step(self, n: int = 1):
