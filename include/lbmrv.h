@@ -305,9 +305,43 @@ LBMRV_API int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, siz
                             const float* dL_dS_dev, float* dL_dS0_dev, double* dL_ds_host,
                             double* dL_damp_host, float* dL_dut0_dev);
 
+/* The reverse sweep one step at a time, for callers that drive the forward steps themselves
+ * (a slab, whose steps need halo exchanges between them). With the forward S_t =
+ * C_t(P S_{t-1}) and a loss L(S_N): mu_N = J_{C_N}^T dL/dS_N, mu_t = J_{C_t}^T P^T mu_{t+1},
+ * dL/dS_0 = P^T mu_1 (lbmrv_adjoint_gather). */
+
+/* Doubles of the FP64 parameter-gradient accumulators lbmrv_adjoint_step adds to (-1 for a
+ * lattice without adjoint). The caller owns them and zeroes them before the first step. */
+LBMRV_API int64_t lbmrv_adjoint_acc_doubles(lbmrv_t h);
+
+/* One reverse step at time index t >= 1:
+ *   s_prev_dev  S_{t-1} in the handle's storage type and layout (for a slab: with the halo
+ *               layers the forward exchange gave it before step t), 16-byte aligned
+ *   a_dev       gather = 0: dL/dS_t (FP32 [9][n]); gather = 1: mu_{t+1}, whose transpose-pull
+ *               P^T the kernel forms (for a slab: its halo layers filled by
+ *               lbmrv_halo_unpack_adjoint)
+ *   mu_dev      out: mu_t, FP32 [9][n] (for a slab only the own layers are written)
+ *   acc_dev     lbmrv_adjoint_acc_doubles doubles, added to (dL/ds and dL/dA, per block)
+ *   dL_dut0_dev optional FP32 [2][n]: dL/du~0 added to (prescribed mode)
+ * a, mu and s_prev 16-byte aligned, a != mu. A slab reverses its own layers only.
+ * Asynchronous. */
+LBMRV_API int lbmrv_adjoint_step(lbmrv_t h, const void* s_prev_dev, int64_t t,
+                                 const float* a_dev, int gather, float* mu_dev,
+                                 double* acc_dev, float* dL_dut0_dev);
+
+/* Sums of the accumulators: dL_ds_host[9] (0 for the conserved k < 3) and dL_damp_host
+ * (either may be NULL). Synchronous. */
+LBMRV_API int lbmrv_adjoint_acc_sum(lbmrv_t h, const double* acc_dev, double* dL_ds_host,
+                                    double* dL_damp_host);
+
+/* dL/dS_0 = P^T mu_1 into out_dev (FP32 [9][n]; 16-byte aligned, distinct buffers). For a
+ * slab, mu_1's halo layers must have been filled by lbmrv_halo_unpack_adjoint. Asynchronous. */
+LBMRV_API int lbmrv_adjoint_gather(lbmrv_t h, const float* mu_dev, float* out_dev);
+
 /* Kinetic energy L = 1/2 sum_x |q|^2 / rho of the current state (FP64 sum, synchronous)
  * and, when dL_dS_dev (device FP32 [9][nx*ny]) is not NULL, its gradient dL/dS (with
- * respect to the stored values, in FP32 whatever the storage type). */
+ * respect to the stored values, in FP32 whatever the storage type). For a slab, over its
+ * own layers (the gradient is 0 on the halo layers). */
 LBMRV_API int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev);
 
 /* Adjoint of lbmrv_moments at the current state: dL/dS from dL/drho (device FP32 [nx*ny]
@@ -369,8 +403,9 @@ LBMRV_API int lbmrv_halo_map(int lattice, const int64_t dims[3], int side, int64
  * lbmrv_conserved[3] and lbmrv_step_conserved sum the own layers only (the latter by a
  * separate pass); the automatic reference is turned off (a slab needs the shared reference,
  * and lbmrv_init_equilibrium on a slab with the automatic reference is LBMRV_E_INVAL);
- * lbmrv_moments still covers every layer; the adjoint entry points and
- * lbmrv_kinetic_energy return LBMRV_E_UNSUPPORTED. LBMRV_E_INVAL for fewer than 3 layers. */
+ * lbmrv_moments still covers every layer; lbmrv_kinetic_energy and lbmrv_adjoint_step
+ * cover the own layers; lbmrv_forward_checkpointed / lbmrv_adjoint (which step without
+ * exchanges) return LBMRV_E_UNSUPPORTED. LBMRV_E_INVAL for fewer than 3 layers. */
 LBMRV_API int lbmrv_set_slab(lbmrv_t h, int64_t first, int64_t extent);
 
 /* Pack the current state's outgoing face values: send_lo_dev for the neighbour below
@@ -384,6 +419,21 @@ LBMRV_API int lbmrv_halo_pack(lbmrv_t h, void* send_lo_dev, void* send_hi_dev);
  * for its lower face (either may be NULL). Asynchronous. LBMRV_E_INVAL when h is not a
  * slab. */
 LBMRV_API int lbmrv_halo_unpack(lbmrv_t h, const void* recv_lo_dev, const void* recv_hi_dev);
+
+/* The adjoint exchange of a slab's adjoint vector mu (FP32, the state layout), for the
+ * gathers of the reverse sweep: the other way round from the forward exchange. Through the
+ * lower face (side 0) a slab sends layer 1's populations with c = +1 and receives c = -1
+ * populations into layer 0; through the upper face (side 1) it sends layer m-2's c = -1
+ * populations and receives c = +1 populations into layer m-1. As for the forward exchange,
+ * what a slab sends through its upper face its upper neighbour receives through its lower
+ * face. Buffers: FP32, lbmrv_halo_count values each, NULL skips a face. The maps are host
+ * only; pack and unpack are asynchronous; LBMRV_E_INVAL when h is not a slab. */
+LBMRV_API int lbmrv_halo_map_adjoint(int lattice, const int64_t dims[3], int side,
+                                     int64_t* send_idx, int64_t* recv_idx);
+LBMRV_API int lbmrv_halo_pack_adjoint(lbmrv_t h, const float* mu_dev, float* send_lo_dev,
+                                      float* send_hi_dev);
+LBMRV_API int lbmrv_halo_unpack_adjoint(lbmrv_t h, float* mu_dev, const float* recv_lo_dev,
+                                        const float* recv_hi_dev);
 
 /* FP64 sums {sum rho, sum rho u_x, sum rho u_y, sum rho u_z (0 for D2Q9)} of initial fields
  * (laid out as for lbmrv_init_equilibrium; rho_dev NULL: 1) over the handle's own nodes (a

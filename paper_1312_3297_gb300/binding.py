@@ -76,6 +76,13 @@ SIGNATURES = [
     ("lbmrv_halo_unpack", _I, [_VP, _VP, _VP]),
     ("lbmrv_flow_sums", _I, [_VP, _VP, _VP, _DP]),
     ("lbmrv_set_reference_sums", _I, [_VP, _D, _DP]),
+    ("lbmrv_halo_map_adjoint", _I, [_I, _I64P, _I, _VP, _VP]),
+    ("lbmrv_halo_pack_adjoint", _I, [_VP, _VP, _VP, _VP]),
+    ("lbmrv_halo_unpack_adjoint", _I, [_VP, _VP, _VP, _VP]),
+    ("lbmrv_adjoint_acc_doubles", _I64, [_VP]),
+    ("lbmrv_adjoint_step", _I, [_VP, _VP, _I64, _VP, _I, _VP, _VP, _VP]),
+    ("lbmrv_adjoint_acc_sum", _I, [_VP, _VP, _DP, _DP]),
+    ("lbmrv_adjoint_gather", _I, [_VP, _VP, _VP]),
     ("lbmrv_conserved3", _I, [_VP, _DP]),
     ("lbmrv_step_conserved", _I, [_VP, _I64, _DP]),
     ("lbmrv_adjoint_workspace_bytes", _I64, [_VP, _I64, _I64]),
@@ -320,6 +327,51 @@ def lbmrv_halo_map(lattice: int, dims, side: int):
     if rc < 0:
         raise LbmrvError(rc, f"lbmrv_halo_map(side={side})")
     return send, recv
+
+
+def lbmrv_halo_map_adjoint(lattice: int, dims, side: int):
+    """Returns (send_idx, recv_idx) of the adjoint exchange as numpy int64 arrays."""
+    import numpy as np
+
+    count = lbmrv_halo_count(lattice, dims)
+    if count < 0:
+        raise LbmrvError(LBMRV_E_INVAL, f"lbmrv_halo_count: bad slab dims {tuple(dims)}")
+    send = np.empty(count, dtype=np.int64)
+    recv = np.empty(count, dtype=np.int64)
+    rc = load().lbmrv_halo_map_adjoint(int(lattice), _dims(dims), int(side), send.ctypes.data,
+                                       recv.ctypes.data)
+    if rc < 0:
+        raise LbmrvError(rc, f"lbmrv_halo_map_adjoint(side={side})")
+    return send, recv
+
+
+def lbmrv_halo_pack_adjoint(h, mu, send_lo, send_hi) -> None:
+    _check(load().lbmrv_halo_pack_adjoint(h, _addr(mu), _addr(send_lo), _addr(send_hi)), h)
+
+
+def lbmrv_halo_unpack_adjoint(h, mu, recv_lo, recv_hi) -> None:
+    _check(load().lbmrv_halo_unpack_adjoint(h, _addr(mu), _addr(recv_lo), _addr(recv_hi)), h)
+
+
+def lbmrv_adjoint_acc_doubles(h) -> int:
+    return load().lbmrv_adjoint_acc_doubles(h)
+
+
+def lbmrv_adjoint_step(h, s_prev, t: int, a, gather: bool, mu, acc, dL_dut0=None) -> None:
+    _check(load().lbmrv_adjoint_step(h, _addr(s_prev), int(t), _addr(a), int(bool(gather)),
+                                     _addr(mu), _addr(acc), _addr(dL_dut0)), h)
+
+
+def lbmrv_adjoint_acc_sum(h, acc):
+    """Returns (dL/ds as 9 floats, dL/dA)."""
+    ds = (ctypes.c_double * 9)()
+    da = ctypes.c_double()
+    _check(load().lbmrv_adjoint_acc_sum(h, _addr(acc), ds, ctypes.byref(da)), h)
+    return list(ds), da.value
+
+
+def lbmrv_adjoint_gather(h, mu, out) -> None:
+    _check(load().lbmrv_adjoint_gather(h, _addr(mu), _addr(out)), h)
 
 
 def lbmrv_set_slab(h, first: int, extent: int) -> None:

@@ -107,13 +107,14 @@ __global__ void k_moments_vjp(const T* __restrict__ g, const float* __restrict__
     }
 }
 
-// Kinetic energy L = 1/2 sum lambda^2 |j|^2 / rho of a stored state (storage type T;
-// per-block FP64 partials in part[b*4]), and optionally dL/dg_j = lambda^2 (c_j . j / rho -
-// 1/2 |j|^2 / rho^2).
+// Kinetic energy L = 1/2 sum lambda^2 |j|^2 / rho of nodes 0 .. n-1 of a stored state
+// (storage type T, planes `plane` elements apart; per-block FP64 partials in part[b*4]), and
+// optionally dL/dg_j = lambda^2 (c_j . j / rho - 1/2 |j|^2 / rho^2) at those nodes.
 template <typename T>
 __global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const T* __restrict__ g,
                                                                    float* __restrict__ grad,
-                                                                   int64_t n, StoreRef ref,
+                                                                   int64_t n, int64_t plane,
+                                                                   StoreRef ref,
                                                                    float lambda,
                                                                    double* __restrict__ part) {
     float ke = 0.0f;
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const T* __re
          i += (int64_t)gridDim.x * blockDim.x) {
         float h[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) h[j] = to_f(g[j * n + i]);
+        for (int j = 0; j < 9; ++j) h[j] = to_f(g[j * plane + i]);
         const NodeMoments m = node_moments(h);
         const float ir = recip(ref.rho + m.drho);
         const float jx = ref.jx + m.jx, jy = ref.jy + m.jy;
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_kinetic_energy(const T* __re
             for (int j = 0; j < 9; ++j) {
                 const float cx = (float)((j == 1 || j == 5 || j == 8) - (j == 3 || j == 6 || j == 7));
                 const float cy = (float)((j == 2 || j == 5 || j == 6) - (j == 4 || j == 7 || j == 8));
-                grad[j * n + i] = l2 * ((cx * jx + cy * jy) * ir - 0.5f * jj * ir * ir);
+                grad[j * plane + i] = l2 * ((cx * jx + cy * jy) * ir - 0.5f * jj * ir * ir);
             }
         }
     }
@@ -231,20 +232,20 @@ cudaError_t launch_moments_vjp(int storage, const void* g, const float* drho, co
 }
 
 cudaError_t launch_kinetic_energy(int storage, const void* g, float* grad, int64_t n,
-                                  const StoreRef& ref, float lambda, double* partials, int nblk,
-                                  double* out, cudaStream_t st) {
+                                  int64_t plane, const StoreRef& ref, float lambda,
+                                  double* partials, int nblk, double* out, cudaStream_t st) {
     switch (storage) {
         case kStoreF32:
             k_kinetic_energy<<<nblk, kReduceThreads, 0, st>>>(static_cast<const float*>(g), grad,
-                                                              n, ref, lambda, partials);
+                                                              n, plane, ref, lambda, partials);
             break;
         case kStoreF16:
             k_kinetic_energy<<<nblk, kReduceThreads, 0, st>>>(static_cast<const __half*>(g), grad,
-                                                              n, ref, lambda, partials);
+                                                              n, plane, ref, lambda, partials);
             break;
         case kStoreBF16:
             k_kinetic_energy<<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __nv_bfloat16*>(g), grad, n, ref, lambda, partials);
+                static_cast<const __nv_bfloat16*>(g), grad, n, plane, ref, lambda, partials);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -185,7 +185,8 @@ __device__ __forceinline__ void adjoint_pack(const T* __restrict__ s_prev,
 
 // One reverse step, persistent, with the work balanced across the resident warps. A warp
 // item is 32 consecutive packs of one row (`chunks` items per row); warp w of W takes items
-// [w I / W, (w + 1) I / W) of the I = chunks * ny in row order, so every warp holds the same
+// [w I / W, (w + 1) I / W) of the I = chunks * (y1 - y0) of rows [y0, y1) (all rows, or a
+// slab's own rows) in row order, so every warp holds the same
 // number of items to within one and the grid (every block resident at once) ends nearly
 // together. A grid of whole rows per block leaves its last wave part-empty when the rows
 // do not fill a whole number of waves (1024^2: 3.4 waves).
@@ -199,9 +200,10 @@ __global__ void __launch_bounds__(kAdjThreads, NV >= 4 ? 3 : 4)
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (kAdjThreads / 32);
     const int64_t w = (int64_t)blockIdx.x * (kAdjThreads / 32) + (threadIdx.x >> 5);
-    const int64_t items = (int64_t)chunks * aa.step.ny;
+    const int64_t items = (int64_t)chunks * (aa.y1 - aa.y0);
     const int64_t i0 = w * items / warps, i1 = (w + 1) * items / warps;
     int y = (int)(i0 / chunks), c = (int)(i0 - (int64_t)y * chunks);
+    y += aa.y0;
     float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int64_t it = i0; it < i1; ++it) {  // warp-uniform bounds: shuffles stay full-mask
         PackLane p;
@@ -246,7 +248,8 @@ template <typename T, int NV, int UM, bool GATHER>
 cudaError_t adjoint_launch(const T* s_prev, const float* a_in, float* mu_out,
                            const AdjointArgs& aa, cudaStream_t st) {
     const int chunks = (aa.step.nx + 32 * NV - 1) / (32 * NV);
-    const int64_t items = (int64_t)chunks * aa.step.ny;
+    const int64_t items = (int64_t)chunks * (aa.y1 - aa.y0);
+    if (items <= 0) return cudaErrorInvalidValue;
     const int64_t nb = balanced_blocks(k_adjoint_step_bal<T, NV, UM, GATHER>, items);
     if (nb < 1) return cudaErrorInvalidConfiguration;
     // the accumulators hold one slot per block of adjoint_grid, never fewer than nb

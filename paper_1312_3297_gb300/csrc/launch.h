@@ -89,6 +89,7 @@ struct AdjointArgs {
     float da_factor;   // d(u~/lambda)/dA = cos(2 pi k / P) / lambda for dL/dA
     float* dut0;       // optional [2][n]: accumulates amp_t * dL/d(u~/lambda) per node
     double* acc;       // per-block FP64 accumulators, 8 per block (6 rates, dL/dA, unused)
+    int y0 = 0, y1 = 0;  // rows reversed: [y0, y1) (a slab's own rows; else 0 .. ny)
 };
 
 dim3 adjoint_grid(int nx, int ny, int nv);
@@ -111,8 +112,9 @@ cudaError_t launch_moments_vjp(int storage, const void* g, const float* drho, co
                                float* out, int64_t n, const StoreRef& ref, float lambda,
                                cudaStream_t st);
 // partials: 4 * nblk doubles of scratch (slot 0 of each used); out: 1 double (device).
+// Over nodes 0 .. n-1 of g (and grad), planes `plane` elements apart.
 cudaError_t launch_kinetic_energy(int storage, const void* g, float* grad, int64_t n,
-                                  const StoreRef& ref, float lambda, double* partials, int nblk,
-                                  double* out, cudaStream_t st);
+                                  int64_t plane, const StoreRef& ref, float lambda,
+                                  double* partials, int nblk, double* out, cudaStream_t st);
 
 }  // namespace lbmrv

@@ -167,6 +167,8 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
             aa.da_factor = (float)(time_factor(h, t0 + k) / h->lambda);
             aa.dut0 = dL_dut0_dev;
             aa.acc = acc;
+            aa.y0 = 0;
+            aa.y1 = (int)h->ny;
             e = launch_adjoint_step(h->storage, um, anv, s_prev, a, gather, mu[pp], aa,
                                     h->stream);
             a = mu[pp];
@@ -189,16 +191,85 @@ int lbmrv_adjoint(lbmrv_t h, int64_t n, int64_t seg, void* ws_dev, size_t ws_byt
     return LBMRV_OK;
 }
 
-int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
-    if (!h || !ke_host) return fail(h, LBMRV_E_INVAL, "lbmrv_kinetic_energy: NULL argument");
-    if (h->lattice != LBMRV_D2Q9 || h->slab)
-        return fail(h, LBMRV_E_UNSUPPORTED,
-                    "lbmrv_kinetic_energy: needs a D2Q9 handle that is not a slab");
+int64_t lbmrv_adjoint_acc_doubles(lbmrv_t h) {
+    if (!h || h->lattice != LBMRV_D2Q9) return -1;
+    return 8 * (adjoint_blocks((int)h->nx, (int)h->ny, adjoint_nv(h)) + 1);
+}
+
+int lbmrv_adjoint_step(lbmrv_t h, const void* s_prev_dev, int64_t t, const float* a_dev,
+                       int gather, float* mu_dev, double* acc_dev, float* dL_dut0_dev) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_adjoint_step: NULL handle");
+    if (h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_adjoint_step: needs a D2Q9 handle");
+    if (!s_prev_dev || !a_dev || !mu_dev || !acc_dev || t < 1)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_adjoint_step: NULL buffer or t < 1");
+    // the kernel reads and writes the adjoint vectors, and reads the state, in 16-byte packs
+    if (reinterpret_cast<uintptr_t>(a_dev) % 16 || reinterpret_cast<uintptr_t>(mu_dev) % 16 ||
+        reinterpret_cast<uintptr_t>(s_prev_dev) % 16 || a_dev == mu_dev)
+        return fail(h, LBMRV_E_INVAL,
+                    "lbmrv_adjoint_step: buffers must be distinct and 16-byte aligned");
+    DeviceGuard g(h->device);
+    AdjointArgs aa;
+    aa.step = make_args(h, t);
+    aa.da_factor = (float)(time_factor(h, t) / h->lambda);
+    aa.dut0 = dL_dut0_dev;
+    aa.acc = acc_dev;
+    aa.y0 = h->slab ? 1 : 0;  // a slab reverses its own rows only
+    aa.y1 = h->slab ? (int)h->ny - 1 : (int)h->ny;
+    const cudaError_t e = launch_adjoint_step(h->storage, kernel_mode(h), adjoint_nv(h),
+                                              s_prev_dev, a_dev, gather != 0, mu_dev, aa,
+                                              h->stream);
+    return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_adjoint_step");
+}
+
+int lbmrv_adjoint_acc_sum(lbmrv_t h, const double* acc_dev, double* dL_ds_host,
+                          double* dL_damp_host) {
+    if (!h || !acc_dev) return fail(h, LBMRV_E_INVAL, "lbmrv_adjoint_acc_sum: NULL argument");
+    if (h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_adjoint_acc_sum: needs a D2Q9 handle");
     DeviceGuard g(h->device);
     double* res = h->red + 8 * (size_t)h->red_blocks;
-    cudaError_t e = launch_kinetic_energy(h->storage, h->f[h->cur], dL_dS_dev, h->n,
-                                          store_ref(h), (float)h->lambda, h->red,
-                                          h->red_blocks, res, h->stream);
+    double out[8] = {0};
+    cudaError_t e = launch_acc_final(acc_dev, lbmrv_adjoint_acc_doubles(h) / 8 - 1, res,
+                                     h->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, res, sizeof(out), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "lbmrv_adjoint_acc_sum");
+    if (dL_ds_host) {
+        dL_ds_host[0] = dL_ds_host[1] = dL_ds_host[2] = 0.0;
+        for (int k = 0; k < 6; ++k) dL_ds_host[3 + k] = out[k];
+    }
+    if (dL_damp_host) *dL_damp_host = out[6];
+    return LBMRV_OK;
+}
+
+int lbmrv_adjoint_gather(lbmrv_t h, const float* mu_dev, float* out_dev) {
+    if (!h || !mu_dev || !out_dev || mu_dev == out_dev)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_adjoint_gather: NULL or aliased buffers");
+    if (reinterpret_cast<uintptr_t>(mu_dev) % 16 || reinterpret_cast<uintptr_t>(out_dev) % 16)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_adjoint_gather: buffers must be 16-byte aligned");
+    DeviceGuard g(h->device);
+    const cudaError_t e = launch_gather(mu_dev, out_dev, (int)h->nx, (int)h->ny, h->stream);
+    return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_adjoint_gather");
+}
+
+int lbmrv_kinetic_energy(lbmrv_t h, double* ke_host, float* dL_dS_dev) {
+    if (!h || !ke_host) return fail(h, LBMRV_E_INVAL, "lbmrv_kinetic_energy: NULL argument");
+    if (h->lattice != LBMRV_D2Q9)
+        return fail(h, LBMRV_E_UNSUPPORTED, "lbmrv_kinetic_energy: needs a D2Q9 handle");
+    DeviceGuard g(h->device);
+    double* res = h->red + 8 * (size_t)h->red_blocks;
+    cudaError_t e = cudaSuccess;
+    if (h->slab && dL_dS_dev)  // the halo layers are not part of the loss
+        e = cudaMemsetAsync(dL_dS_dev, 0, sizeof(float) * 9 * (size_t)h->n, h->stream);
+    const int64_t o = owned_first(h);
+    if (e == cudaSuccess)
+        e = launch_kinetic_energy(h->storage,
+                                  static_cast<const char*>(h->f[h->cur]) + o * elem_size(h->storage),
+                                  dL_dS_dev ? dL_dS_dev + o : nullptr, owned_count(h), h->n,
+                                  store_ref(h), (float)h->lambda, h->red, h->red_blocks, res,
+                                  h->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ke_host, res, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);

@@ -82,6 +82,18 @@ Face recv_face(int lattice, int64_t m, int side) {
     return side == 0 ? Face{0, crossing(lattice, +1)} : Face{m - 1, crossing(lattice, -1)};
 }
 
+// The adjoint exchange runs the other way. The reverse step gathers mu_{k+1}(x + c_j) (the
+// transpose of the pull), so an edge layer needs from the halo layer beyond it the
+// populations whose velocity points out through that face: the lower face sends layer 1's
+// c = +1 populations and receives c = -1 populations into layer 0; the upper face sends
+// layer m-2's c = -1 populations and receives c = +1 populations into layer m-1.
+Face send_face_adjoint(int lattice, int64_t m, int side) {
+    return side == 0 ? Face{1, crossing(lattice, +1)} : Face{m - 2, crossing(lattice, -1)};
+}
+Face recv_face_adjoint(int lattice, int64_t m, int side) {
+    return side == 0 ? Face{0, crossing(lattice, -1)} : Face{m - 1, crossing(lattice, +1)};
+}
+
 // Copies between the two face buffers and the state, value b of face f (blockIdx.y) <->
 // state[j_k n + layer L + i]. PACK: buffers <- state; otherwise state <- buffers. E: an
 // unsigned type of the storage element's size (the values are moved as bits). A NULL
@@ -109,18 +121,19 @@ __global__ void k_halo_copy(E* __restrict__ state, E* __restrict__ buf_lo,
     }
 }
 
-// Both faces in one launch (grid y = face).
+// Both faces in one launch (grid y = face), between `state` (elements of `elem` bytes, the
+// handle's layout) and the two buffers.
 template <bool PACK>
-cudaError_t halo_copy(const lbmrv_s* h, void* buf_lo, void* buf_hi, const Face& lo,
-                      const Face& hi) {
+cudaError_t halo_copy(const lbmrv_s* h, void* state, int64_t elem, void* buf_lo,
+                      void* buf_hi, const Face& lo, const Face& hi) {
     const int64_t L = layer_size(h), total = (int64_t)lo.pops.count * L;
     const dim3 grid((unsigned)grid_stride_blocks(total, 256), 2);
-    if (elem_size(h->storage) == 4)
+    if (elem == 4)
         return launch_pdl(k_halo_copy<uint32_t, PACK>, grid, dim3(256), h->stream,
-                          static_cast<uint32_t*>(h->f[h->cur]), static_cast<uint32_t*>(buf_lo),
+                          static_cast<uint32_t*>(state), static_cast<uint32_t*>(buf_lo),
                           static_cast<uint32_t*>(buf_hi), h->n, L, lo, hi);
     return launch_pdl(k_halo_copy<uint16_t, PACK>, grid, dim3(256), h->stream,
-                      static_cast<uint16_t*>(h->f[h->cur]), static_cast<uint16_t*>(buf_lo),
+                      static_cast<uint16_t*>(state), static_cast<uint16_t*>(buf_lo),
                       static_cast<uint16_t*>(buf_hi), h->n, L, lo, hi);
 }
 
@@ -180,8 +193,8 @@ int lbmrv_halo_pack(lbmrv_t h, void* send_lo_dev, void* send_hi_dev) {
     DeviceGuard g(h->device);
     const int64_t m = layer_count(h);
     if (!send_lo_dev && !send_hi_dev) return LBMRV_OK;
-    const cudaError_t e = halo_copy<true>(h, send_lo_dev, send_hi_dev,
-                                          send_face(h->lattice, m, 0),
+    const cudaError_t e = halo_copy<true>(h, h->f[h->cur], elem_size(h->storage), send_lo_dev,
+                                          send_hi_dev, send_face(h->lattice, m, 0),
                                           send_face(h->lattice, m, 1));
     return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_halo_pack");
 }
@@ -193,11 +206,55 @@ int lbmrv_halo_unpack(lbmrv_t h, const void* recv_lo_dev, const void* recv_hi_de
     DeviceGuard g(h->device);
     const int64_t m = layer_count(h);
     if (!recv_lo_dev && !recv_hi_dev) return LBMRV_OK;
-    const cudaError_t e = halo_copy<false>(h, const_cast<void*>(recv_lo_dev),
+    const cudaError_t e = halo_copy<false>(h, h->f[h->cur], elem_size(h->storage),
+                                           const_cast<void*>(recv_lo_dev),
                                            const_cast<void*>(recv_hi_dev),
                                            recv_face(h->lattice, m, 0),
                                            recv_face(h->lattice, m, 1));
     return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_halo_unpack");
+}
+
+int lbmrv_halo_map_adjoint(int lattice, const int64_t dims[3], int side, int64_t* send_idx,
+                           int64_t* recv_idx) {
+    int64_t L, m, n;
+    if (!slab_shape(lattice, dims, &L, &m, &n) || (side != 0 && side != 1))
+        return LBMRV_E_INVAL;
+    const Face fs = send_face_adjoint(lattice, m, side), fr = recv_face_adjoint(lattice, m, side);
+    for (int k = 0; k < fs.pops.count; ++k)
+        for (int64_t i = 0; i < L; ++i) {
+            if (send_idx) send_idx[k * L + i] = (int64_t)fs.pops.j[k] * n + fs.layer * L + i;
+            if (recv_idx) recv_idx[k * L + i] = (int64_t)fr.pops.j[k] * n + fr.layer * L + i;
+        }
+    return LBMRV_OK;
+}
+
+int lbmrv_halo_pack_adjoint(lbmrv_t h, const float* mu_dev, float* send_lo_dev,
+                            float* send_hi_dev) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_halo_pack_adjoint: NULL handle");
+    if (!h->slab || !mu_dev)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_halo_pack_adjoint: not a slab, or NULL mu");
+    if (!send_lo_dev && !send_hi_dev) return LBMRV_OK;
+    DeviceGuard g(h->device);
+    const int64_t m = layer_count(h);
+    const cudaError_t e = halo_copy<true>(h, const_cast<float*>(mu_dev), 4, send_lo_dev,
+                                          send_hi_dev, send_face_adjoint(h->lattice, m, 0),
+                                          send_face_adjoint(h->lattice, m, 1));
+    return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_halo_pack_adjoint");
+}
+
+int lbmrv_halo_unpack_adjoint(lbmrv_t h, float* mu_dev, const float* recv_lo_dev,
+                              const float* recv_hi_dev) {
+    if (!h) return fail(nullptr, LBMRV_E_INVAL, "lbmrv_halo_unpack_adjoint: NULL handle");
+    if (!h->slab || !mu_dev)
+        return fail(h, LBMRV_E_INVAL, "lbmrv_halo_unpack_adjoint: not a slab, or NULL mu");
+    if (!recv_lo_dev && !recv_hi_dev) return LBMRV_OK;
+    DeviceGuard g(h->device);
+    const int64_t m = layer_count(h);
+    const cudaError_t e = halo_copy<false>(h, mu_dev, 4, const_cast<float*>(recv_lo_dev),
+                                           const_cast<float*>(recv_hi_dev),
+                                           recv_face_adjoint(h->lattice, m, 0),
+                                           recv_face_adjoint(h->lattice, m, 1));
+    return e == cudaSuccess ? LBMRV_OK : cuda_fail(h, e, "lbmrv_halo_unpack_adjoint");
 }
 
 int lbmrv_flow_sums(lbmrv_t h, const float* rho_dev, const float* u_dev, double out_host[4]) {

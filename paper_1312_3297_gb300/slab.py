@@ -12,6 +12,8 @@ plan and index maps. This module only moves buffers between ranks and calls the 
 """
 from __future__ import annotations
 
+import math
+
 import torch
 
 from . import binding as B
@@ -71,6 +73,10 @@ class Slab:
         dev, dt = self.sim.device, self.sim.dtype
         self.send_lo, self.send_hi, self.recv_lo, self.recv_hi = (
             torch.empty(n_face, dtype=dt, device=dev) for _ in range(4))
+        # the adjoint exchange's buffers (FP32 adjoint vectors)
+        self.a_send_lo, self.a_send_hi, self.a_recv_lo, self.a_recv_hi = (
+            torch.empty(n_face, dtype=torch.float32, device=dev) for _ in range(4))
+        self._fields = None
 
     # -- lifecycle
     def close(self):
@@ -98,6 +104,7 @@ class Slab:
                               self._comm_device(), self.group)
         B.lbmrv_set_reference_sums(self.sim.h, self.sim.rho_ref, sums)
         self.sim.init_equilibrium(rho, *u)
+        self._fields = (rho, u)  # for the adjoint of the initialisation
 
     def _comm_device(self):
         import torch.distributed as dist
@@ -120,6 +127,70 @@ class Slab:
         for _ in range(int(n)):
             self.exchange()
             self.sim.step(1)
+
+    def exchange_adjoint(self, mu):
+        """Fill the halo layers of the adjoint vector mu (FP32, the state's shape) with the
+        neighbours' values that the reverse step's gathers read."""
+        h = self.sim.h
+        if self.world == 1:  # its own neighbour: pack straight into the other face's halo
+            B.lbmrv_halo_pack_adjoint(h, mu, self.a_recv_hi, self.a_recv_lo)
+        else:
+            B.lbmrv_halo_pack_adjoint(h, mu, self.a_send_lo, self.a_send_hi)
+            exchange_faces(self.a_send_lo, self.a_send_hi, self.a_recv_lo, self.a_recv_hi,
+                           self.rank, self.world, self.group)
+        B.lbmrv_halo_unpack_adjoint(h, mu, self.a_recv_lo, self.a_recv_hi)
+
+    def kinetic_energy_gradient(self, n: int, seg: int = 0):
+        """Advance n steps from the state set by init_equilibrium (time 0) with a checkpoint
+        every seg steps (sqrt(n) when 0), and return the kinetic energy L of the final state
+        and its gradients: (L, dL/du0 of the own layers [d, count, ...], dL/ds [q], dL/dA).
+        L, dL/ds and dL/dA are FP64 sums over the slabs (all-reduced). The reverse sweep
+        recomputes each segment from its checkpoint, with the forward exchanges, and
+        exchanges the adjoint vector before each gather. The handle ends at the final
+        state (time n)."""
+        sim, h = self.sim, self.sim.h
+        if self._fields is None or sim.time != 0:
+            raise ValueError("kinetic_energy_gradient starts from init_equilibrium (time 0)")
+        n = int(n)
+        seg = int(seg) if seg else max(1, int(math.ceil(math.sqrt(n))))
+        # forward: checkpoints are the states as the steps read them (halos exchanged)
+        ck = []
+        for k in range(1, n + 1):
+            self.exchange()
+            if (k - 1) % seg == 0:
+                ck.append(sim.state())
+            sim.step(1)
+        final = sim.state()
+        ke, dlds = sim.kinetic_energy(grad=True)
+        dev = sim.device
+        acc = torch.zeros(B.lbmrv_adjoint_acc_doubles(h), dtype=torch.float64, device=dev)
+        mu = [torch.empty_like(dlds) for _ in range(2)]
+        a, gather, pp = dlds, False, 0
+        for c in range(len(ck) - 1, -1, -1):
+            base = c * seg
+            khi = min(base + seg, n)
+            states = [ck[c]]
+            if khi - base > 1:  # recompute the segment's states, with their exchanges
+                sim.set_state(ck[c], base)
+                for _ in range(base + 1, khi):
+                    sim.step(1)
+                    self.exchange()
+                    states.append(sim.state())
+            for k in range(khi, base, -1):
+                if gather:
+                    self.exchange_adjoint(a)
+                B.lbmrv_adjoint_step(h, states[k - 1 - base], k, a, gather, mu[pp], acc)
+                a, gather, pp = mu[pp], True, pp ^ 1
+        self.exchange_adjoint(a)
+        d0 = torch.empty_like(dlds)
+        B.lbmrv_adjoint_gather(h, a, d0)
+        ds, da = B.lbmrv_adjoint_acc_sum(h, acc)
+        rho, u = self._fields
+        _, du = sim.equilibrium_vjp(rho, u, d0)
+        sim.set_state(final, n)
+        tot = allreduce_sums([ke] + list(ds) + [da], self.world, self._comm_device(),
+                             self.group)
+        return tot[0], du[:, 1:-1].contiguous(), tot[1:1 + len(ds)], tot[-1]
 
     # -- results
     def conserved3(self):

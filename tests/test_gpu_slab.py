@@ -199,7 +199,135 @@ def test_slab_calls_reject_misuse():
     with pytest.raises(B.LbmrvError):  # a slab needs the shared reference
         sim.init_equilibrium(*(torch.as_tensor(d[k], dtype=torch.float32)
                                for k in ("rho", "ux", "uy")))
-    with pytest.raises(B.LbmrvError) as ei:
-        sim.kinetic_energy()
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    with pytest.raises(B.LbmrvError) as ei:  # it would step without the exchanges
+        B.lbmrv_forward_checkpointed(sim.h, 4, 2, ws, ws.numel())
     assert ei.value.status == B.LBMRV_E_UNSUPPORTED
     sim.close()
+
+
+def _single_gradient(nx, ny, mode, steps, seg, fields, u_ref, ut0=None):
+    """Kinetic-energy gradient of the single handle (lbmrv_forward_checkpointed +
+    lbmrv_adjoint) with a fixed reference: (L, dL/du0 [2, ny, nx], dL/ds, dL/dA)."""
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9
+
+    sim = D2Q9(nx, ny, S_PAPER, mode=mode, u_ref=u_ref)
+    if mode == "prescribed":
+        sim.set_utilde(None if ut0 is None else torch.as_tensor(ut0), AMP, PERIOD)
+    rho = torch.as_tensor(fields[0], device="cuda")
+    u = torch.stack([torch.as_tensor(c, device="cuda") for c in fields[1:]]).contiguous()
+    sim.init_equilibrium(rho, u[0], u[1])
+    ws = sim.adjoint_workspace(steps, seg)
+    sim.forward_checkpointed(steps, seg, ws)
+    ke, dlds = sim.kinetic_energy(grad=True)
+    d0, ds, da, _ = sim.adjoint(steps, seg, ws, dlds)
+    _, du0 = sim.equilibrium_vjp(rho, u, d0)
+    out = (ke, du0.cpu().numpy(), ds, da)
+    sim.close()
+    return out
+
+
+@pytest.mark.parametrize("mode", ["fluid", "prescribed", "zero"])
+def test_slab_driver_gradient_equals_the_single_handle(mode):
+    """The Slab driver's reverse sweep (one rank, its own neighbour; checkpoints every 6
+    steps with recomputation; adjoint exchanges before every gather) against the single
+    handle's lbmrv_adjoint: dL/du0 bit for bit (the same per-node arithmetic), the loss and
+    the parameter gradients (sums in another order) to 1e-9 and 1e-6."""
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9, binding as B
+    from paper_1312_3297_gb300.slab import Slab
+
+    nx, ny, steps, seg = 64, 40, 40, 6
+    rho, ux, uy = (a.astype(np.float32) for a in f32_fields(inp.noisy_shear_wave(nx, ny, seed=2)))
+    sl = Slab(D2Q9, (nx, ny), S_PAPER, mode=mode)
+    if mode == "prescribed":
+        sl.sim.set_utilde(None, AMP, PERIOD)
+    sl.init_equilibrium(torch.as_tensor(rho), torch.as_tensor(ux), torch.as_tensor(uy))
+    ke, du0, ds, da = sl.kinetic_energy_gradient(steps, seg)
+    U = B.lbmrv_get_reference(sl.sim.h)[1][:2]
+    assert sl.time == steps
+    sl.close()
+    ke1, du1, ds1, da1 = _single_gradient(nx, ny, mode, steps, seg, (rho, ux, uy), U)
+    np.testing.assert_array_equal(du0.cpu().numpy(), du1)
+    assert abs(ke - ke1) <= 1e-9 * abs(ke1)
+    np.testing.assert_allclose(ds, ds1, rtol=1e-6, atol=1e-12)
+    assert abs(da - da1) <= 1e-6 * max(abs(da1), 1e-30)
+
+
+def test_two_slab_handles_reverse_sweep_equals_the_single_handle():
+    """Two slab handles on one GPU (64^2, rows 32 + 32) run the forward steps with the
+    forward exchange and the reverse sweep with the adjoint exchange, one device copy per
+    face buffer each way, every state checkpointed: dL/du0 of the stitched own rows equals
+    the single handle's bit for bit; dL/ds and dL/dA, summed over the slabs, to 1e-6."""
+    import torch
+
+    from paper_1312_3297_gb300 import D2Q9, binding as B
+
+    nx = ny = 64
+    steps = 30
+    rho, ux, uy = (a.astype(np.float32) for a in f32_fields(inp.noisy_shear_wave(nx, ny, seed=3)))
+    slabs, sums = _two_slabs(D2Q9, (nx, ny), S_PAPER, "prescribed", "fp32", (rho, ux, uy))
+    a, b = slabs
+    states = {0: [], 1: []}
+    for _ in range(steps):  # forward, keeping every state as its step reads it
+        for sl in slabs:
+            B.lbmrv_halo_pack(sl["sim"].h, sl["bufs"][0], sl["bufs"][1])
+        a["bufs"][2].copy_(b["bufs"][1])
+        a["bufs"][3].copy_(b["bufs"][0])
+        b["bufs"][2].copy_(a["bufs"][1])
+        b["bufs"][3].copy_(a["bufs"][0])
+        for r, sl in enumerate(slabs):
+            B.lbmrv_halo_unpack(sl["sim"].h, sl["bufs"][2], sl["bufs"][3])
+            states[r].append(sl["sim"].state())
+            sl["sim"].step(1)
+    grads = []
+    for sl in slabs:
+        ke, dlds = sl["sim"].kinetic_energy(grad=True)
+        acc = torch.zeros(B.lbmrv_adjoint_acc_doubles(sl["sim"].h), dtype=torch.float64,
+                          device="cuda")
+        mu = [torch.empty_like(dlds) for _ in range(2)]
+        abuf = [torch.empty(3 * nx, device="cuda") for _ in range(4)]
+        grads.append(dict(ke=ke, a=dlds, acc=acc, mu=mu, abuf=abuf, pp=0))
+
+    def adjoint_exchange():
+        for sl, gr in zip(slabs, grads):
+            B.lbmrv_halo_pack_adjoint(sl["sim"].h, gr["a"], gr["abuf"][0], gr["abuf"][1])
+        ga, gb = grads
+        ga["abuf"][2].copy_(gb["abuf"][1])  # a.recv_lo <- b.send_hi
+        ga["abuf"][3].copy_(gb["abuf"][0])  # a.recv_hi <- b.send_lo
+        gb["abuf"][2].copy_(ga["abuf"][1])
+        gb["abuf"][3].copy_(ga["abuf"][0])
+        for sl, gr in zip(slabs, grads):
+            B.lbmrv_halo_unpack_adjoint(sl["sim"].h, gr["a"], gr["abuf"][2], gr["abuf"][3])
+
+    for k in range(steps, 0, -1):
+        if k < steps:
+            adjoint_exchange()
+        for r, (sl, gr) in enumerate(zip(slabs, grads)):
+            out = gr["mu"][gr["pp"]]
+            B.lbmrv_adjoint_step(sl["sim"].h, states[r][k - 1], k, gr["a"], k < steps, out,
+                                 gr["acc"])
+            gr["a"], gr["pp"] = out, gr["pp"] ^ 1
+    adjoint_exchange()
+    du, ds, da, ke = [], np.zeros(9), 0.0, 0.0
+    for sl, gr in zip(slabs, grads):
+        d0 = torch.empty_like(gr["a"])
+        B.lbmrv_adjoint_gather(sl["sim"].h, gr["a"], d0)
+        _, g = sl["sim"].equilibrium_vjp(sl["rho"], sl["u"], d0)
+        du.append(g[:, 1:-1])
+        s_, a_ = B.lbmrv_adjoint_acc_sum(sl["sim"].h, gr["acc"])
+        ds += np.asarray(s_)
+        da += a_
+        ke += gr["ke"]
+    du = torch.cat(du, dim=1).cpu().numpy()
+    U = B.lbmrv_get_reference(a["sim"].h)[1][:2]
+    for sl in slabs:
+        sl["sim"].close()
+    ke1, du1, ds1, da1 = _single_gradient(nx, ny, "prescribed", steps, 1, (rho, ux, uy), U)
+    np.testing.assert_array_equal(du, du1)
+    assert abs(ke - ke1) <= 1e-9 * abs(ke1)
+    np.testing.assert_allclose(ds, ds1, rtol=1e-6, atol=1e-12)
+    assert abs(da - da1) <= 1e-6 * abs(da1)

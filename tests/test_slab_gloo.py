@@ -201,3 +201,32 @@ def test_halo_maps_pair_faces_and_name_crossing_populations():
                 assert sorted(set(j)) == [k for k in range(q) if axis_v[k] == c]
         assert B.lbmrv_halo_count(lat, dims[:1] + (2,) + dims[2:]
                                   if lat == B.LBMRV_D2Q9 else dims[:2] + (2,)) == -1
+
+
+def test_adjoint_halo_maps_run_the_other_way():
+    """The adjoint exchange feeds the reverse step's gathers, mu(x + c_j): through the lower
+    face a slab sends layer 1's c = +1 populations and receives c = -1 populations into
+    layer 0; through the upper face it sends layer m-2's c = -1 populations and receives
+    c = +1 populations into layer m-1. So what the lower face sends is what the lower
+    neighbour's upper face receives (the same populations), as in the forward exchange."""
+    sys.path.insert(0, ROOT)
+    from paper_1312_3297_gb300 import binding as B
+
+    vy2 = [0, 0, 1, 0, -1, 1, 1, -1, -1]
+    vz3 = [0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1]
+    for lat, dims, axis_v, L in [(B.LBMRV_D2Q9, (7, 5, 1), vy2, 7),
+                                 (B.LBMRV_D3Q19, (3, 4, 6), vz3, 12)]:
+        m = dims[1] if lat == B.LBMRV_D2Q9 else dims[2]
+        n = L * m
+        maps = [B.lbmrv_halo_map_adjoint(lat, dims, side) for side in (0, 1)]
+        expect = [(1, +1, 0, -1), (m - 2, -1, m - 1, +1)]
+        for (send, recv), (sl, sc, rl, rc) in zip(maps, expect):
+            for idx, layer, c in ((send, sl, sc), (recv, rl, rc)):
+                j, rest = idx // n, idx % n
+                assert all(axis_v[k] == c for k in j)
+                assert np.all(rest // L == layer)
+                assert np.all(rest % L == np.tile(np.arange(L), len(set(j))))
+        # the buffer sent through one face is received through the other face of the
+        # neighbour: the same populations in the same order
+        assert np.array_equal(maps[0][0] // n, maps[1][1] // n)
+        assert np.array_equal(maps[1][0] // n, maps[0][1] // n)
