@@ -74,32 +74,16 @@ __device__ __forceinline__ void prescribed_grads(float ubx, float uby, float bx,
     }
 }
 
-// The reverse step on one pack of row y (lane geometry p): pull S_{k-1} (stored as T: FP32,
-// or 16-bit values widened to FP32), gather mu_{k+1}
-// (or read dL/dS_N aligned), reverse each node's relaxation, store mu_k. Packs of two or more
-// nodes reverse node pairs with packed FP32 instructions (two nodes per instruction), so 2-
-// and 4-node packs give the same bits; one-node packs use the scalar form (F1) of the same
-// arithmetic, which agrees with them to rounding.
-template <typename T, int NV, int UM, bool GATHER>
-__device__ __forceinline__ void adjoint_pack(const T* __restrict__ s_prev,
-                                             const float* __restrict__ a_in,
-                                             float* __restrict__ mu_out, const AdjointArgs& aa,
-                                             int y, const PackLane& p, float acc[7]) {
+// The reverse relaxation of one pack from its pulled state g and adjoint input adj; stores
+// mu_k.
+template <int NV, int UM>
+__device__ __forceinline__ void adjoint_pack_relax(float g[9][NV], const float adj[9][NV],
+                                                   float* __restrict__ mu_out,
+                                                   const AdjointArgs& aa, int y,
+                                                   const PackLane& p, float acc[7]) {
     const StepArgs& a = aa.step;
-    const int nx = a.nx, ny = a.ny;
-    const int64_t n = (int64_t)nx * ny;
-    const int ym = y == 0 ? ny - 1 : y - 1;
-    const int yp = y == ny - 1 ? 0 : y + 1;
-    const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
-    float g[9][NV], adj[9][NV];
-    pull_pack<T, NV>(s_prev, n, r0, rm, rp, p, g);
-    if (GATHER) {
-        gather_pack<float, NV>(a_in, n, r0, rm, rp, p, adj);
-    } else {
-#pragma unroll
-        for (int j = 0; j < 9; ++j) load_pack<float, NV>(a_in + j * n + r0 + p.x0, p.act, adj[j]);
-    }
-    if (!p.act) return;
+    const int64_t n = (int64_t)a.nx * a.ny;
+    const int64_t r0 = (int64_t)y * a.nx;
     const float cy = UM == UM_ANALYTIC ? cospif(a.two_over_ny * (float)(y + a.y_off)) : 0.0f;
     constexpr bool kPrescribed = UM == UM_ANALYTIC || UM == UM_FIELD;
     if constexpr (NV >= 2) {
@@ -183,6 +167,44 @@ __device__ __forceinline__ void adjoint_pack(const T* __restrict__ s_prev,
     for (int j = 0; j < 9; ++j) store_pack<float, NV>(mu_out + j * n + r0 + p.x0, g[j]);
 }
 
+// The adjoint input of a pack: mu_{k+1} gathered (the transpose of the pull), or dL/dS_N
+// read in place.
+template <int NV, bool GATHER>
+__device__ __forceinline__ void load_adjoint(const float* __restrict__ a_in, int64_t n,
+                                             int64_t r0, int64_t rm, int64_t rp,
+                                             const PackLane& p, float adj[9][NV]) {
+    if constexpr (GATHER) {
+        gather_pack<float, NV>(a_in, n, r0, rm, rp, p, adj);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 9; ++j) load_pack<float, NV>(a_in + j * n + r0 + p.x0, p.act, adj[j]);
+    }
+}
+
+// The reverse step on one pack of row y (lane geometry p): pull S_{k-1} (stored as T: FP32,
+// or 16-bit values widened to FP32), gather mu_{k+1} (or read dL/dS_N aligned), reverse each
+// node's relaxation, store mu_k. Packs of two or more nodes reverse node pairs with packed
+// FP32 instructions (two nodes per instruction), so 2- and 4-node packs give the same bits;
+// one-node packs use the scalar form (F1) of the same arithmetic, which agrees with them to
+// rounding.
+template <typename T, int NV, int UM, bool GATHER>
+__device__ __forceinline__ void adjoint_pack(const T* __restrict__ s_prev,
+                                             const float* __restrict__ a_in,
+                                             float* __restrict__ mu_out, const AdjointArgs& aa,
+                                             int y, const PackLane& p, float acc[7]) {
+    const StepArgs& a = aa.step;
+    const int nx = a.nx, ny = a.ny;
+    const int64_t n = (int64_t)nx * ny;
+    const int ym = y == 0 ? ny - 1 : y - 1;
+    const int yp = y == ny - 1 ? 0 : y + 1;
+    const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
+    float g[9][NV], adj[9][NV];
+    pull_pack<T, NV>(s_prev, n, r0, rm, rp, p, g);
+    load_adjoint<NV, GATHER>(a_in, n, r0, rm, rp, p, adj);
+    if (!p.act) return;
+    adjoint_pack_relax<NV, UM>(g, adj, mu_out, aa, y, p, acc);
+}
+
 // One reverse step, persistent, with the work balanced across the resident warps. A warp
 // item is 32 consecutive packs of one row (`chunks` items per row); warp w of W takes items
 // [w I / W, (w + 1) I / W) of the I = chunks * (y1 - y0) of rows [y0, y1) (all rows, or a
@@ -250,9 +272,9 @@ cudaError_t adjoint_launch(const T* s_prev, const float* a_in, float* mu_out,
     const int chunks = (aa.step.nx + 32 * NV - 1) / (32 * NV);
     const int64_t items = (int64_t)chunks * (aa.y1 - aa.y0);
     if (items <= 0) return cudaErrorInvalidValue;
+    // the accumulators hold one slot per block of adjoint_grid, never fewer than nb
     const int64_t nb = balanced_blocks(k_adjoint_step_bal<T, NV, UM, GATHER>, items);
     if (nb < 1) return cudaErrorInvalidConfiguration;
-    // the accumulators hold one slot per block of adjoint_grid, never fewer than nb
     return launch_pdl(k_adjoint_step_bal<T, NV, UM, GATHER>, dim3((unsigned)nb), dim3(kAdjThreads),
                       st, s_prev, a_in, mu_out, aa, chunks);
 }
