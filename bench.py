@@ -9,7 +9,8 @@ time step (pull transport + relaxation in the moving frame), one kernel launch. 
 ``python bench.py [--gpus N] [--steps K] [--warmup W]`` prints one JSON line.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (same metric).
 With N > 1 (torchrun) every rank advances its own replica of the lattice (weak scaling;
-the step has no exchange across replicas).
+the step has no exchange across replicas). ``--decomp slab`` instead splits one lattice of
+N stacked Taylor-Green cells into slabs, one per rank, with a halo exchange per step.
 """
 from __future__ import annotations
 
@@ -244,6 +245,25 @@ def side_measure(torch, D2Q9, inp, storage, mode, size, fields, steps, peak, u_r
             "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
 
 
+class SlabRun:
+    """The slab driver behind the interface the timed loop uses (step, stream, conserved,
+    close)."""
+
+    def __init__(self, slab):
+        self.slab = slab
+        self.stream = slab.sim.stream
+
+    def step(self, n=1):
+        self.slab.step(n)
+
+    def conserved(self, allow_nonfinite=False):
+        c = self.slab.conserved3()
+        return [c[0], c[1], c[2], c[4]]
+
+    def close(self):
+        self.slab.close()
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -269,6 +289,21 @@ def gpu_arm(args):
         sim.init_equilibrium(torch.as_tensor(d3["rho"], dtype=torch.float32),
                              *(torch.as_tensor(c, dtype=torch.float32) for c in d3["u"]))
         del d3
+    elif args.decomp == "slab":
+        # weak scaling on one lattice of size x (size * world) rows, one slab per rank: N
+        # Taylor-Green cells stacked in y, each rank owning one cell's rows; every step
+        # exchanges the slab faces with the neighbouring ranks
+        from paper_1312_3297_gb300.slab import Slab
+
+        n = size * size
+        fields = inp.taylor_green(size, size, u0=0.04)
+        slab = Slab(D2Q9, (size, size * world), S_RATES, rank=rank, world=world,
+                    mode=args.mode, storage=args.storage)
+        if args.mode == "prescribed":
+            slab.sim.set_utilde(None, UT_AMP, UT_PERIOD)
+        slab.init_equilibrium(*(torch.as_tensor(fields[k], dtype=torch.float32)
+                                for k in ("rho", "ux", "uy")))
+        sim = SlabRun(slab)
     else:
         n = size * size
         fields = inp.taylor_green(size, size, u0=0.04)
@@ -307,7 +342,7 @@ def gpu_arm(args):
     mlups = job_mlups(n, world, args.steps, ms)
     e2e = None
     if not args.no_e2e and size == L and args.storage == "fp32" and args.mode == "prescribed" \
-            and args.lattice == "d2q9":
+            and args.lattice == "d2q9" and args.decomp == "replicas":
         # every rank runs its replica end to end; the job's figure takes the slowest rank
         if world > 1:
             dist.barrier()
@@ -318,7 +353,7 @@ def gpu_arm(args):
     bpn = BYTES_PER_NODE[args.storage] * (19 / 9 if args.lattice == "d3q19" else 1)
     achieved = bpn * n / (per_step_ms * 1e-3) / 1e9
     headline = (size == L and args.storage == "fp32" and args.mode == "prescribed"
-                and args.lattice == "d2q9")
+                and args.lattice == "d2q9" and args.decomp == "replicas")
     out = None
     if rank == 0:
         extras = {}
@@ -366,7 +401,7 @@ def gpu_arm(args):
                        f"{args.lattice} {args.storage} side {size} Taylor-Green, u~ mode {args.mode}",
                        "nodes": n, "bytes_per_node_step": round(bpn, 1),
                        "l2": "state 1.2 GB > 129 MB L2; no flush needed",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"{args.decomp} x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": recorded_traffic() if headline else None,
@@ -375,7 +410,8 @@ def gpu_arm(args):
                          "kernel": kernel_label(args.lattice, args.storage, size, args.mode)},
             "clocks": clock_info,
             "e2e": e2e,
-            "gpu_launches": args.steps * world,  # one step kernel per step and replica
+            # one step kernel per step and rank; a slab adds its pack and unpack kernels
+            "gpu_launches": args.steps * world * (3 if args.decomp == "slab" else 1),
             "cpu_baseline": cpu,
             "modes": extras,
             "wall_ms_timed_region": round(wall_ms, 2),
@@ -782,6 +818,9 @@ def main():
                     help="relative velocity of the timed run (profiling captures)")
     ap.add_argument("--lattice", default="d2q9", choices=["d2q9", "d3q19"],
                     help="lattice of the timed run (d3q19: --size is the cube side)")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1: independent replicas (default), or one lattice of N stacked "
+                         "Taylor-Green cells split into slabs with a halo exchange per step")
     ap.add_argument("--case", default="step", choices=["step", "adjoint"],
                     help="adjoint: only the adjoint workload's timings (profiling captures)")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
