@@ -379,6 +379,7 @@ def gpu_arm(args):
                                                               8192, big, k, peak)
             extras["fp32_fluid_8192"] = side_measure(torch, D2Q9, inp, "fp32", "fluid", 8192,
                                                      big, k, peak)
+            extras["cascaded_geier_16bit_8192"] = cascaded16_measure(torch, big, k, peak)
             del big
             extras["cascaded_geier_fluid"] = cascaded_measure(torch, inp, fields, k, peak)
             extras["conserved_sums_4096"] = sums_measure(torch, D2Q9, inp, fields)
@@ -492,6 +493,26 @@ def cascaded_measure(torch, inp, fields, steps, peak):
     gbs = 72 * n / (per * 1e-3) / 1e9
     return {"mlups": round(n / (per * 1e-3) / 1e6, 1), "ms_per_step": round(per, 5),
             "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+
+
+def cascaded16_measure(torch, big, steps, peak):
+    """Geier's cascaded scheme in FP16 and BF16 storage on the 8192^2 perturbed uniform flow
+    (automatic reference), 36 B per node and step."""
+    from paper_1312_3297_gb300 import D2Q9Cascaded
+
+    out = {}
+    n = 8192 * 8192
+    for st in ("fp16", "bf16"):
+        sim = D2Q9Cascaded(8192, 8192, S_RATES, mode="fluid", storage=st)
+        sim.init_equilibrium(*(torch.as_tensor(big[k], dtype=torch.float32)
+                               for k in ("rho", "ux", "uy")))
+        sim.step(3)
+        per = time_steps(sim, steps, torch) / steps
+        sim.close()
+        gbs = 36 * n / (per * 1e-3) / 1e9
+        out[st] = {"mlups": round(n / (per * 1e-3) / 1e6, 1), "ms_per_step": round(per, 5),
+                   "gbs": round(gbs, 1), "frac": round(gbs / peak, 4)}
+    return out
 
 
 def d3q19_measure(torch, inp, steps, peak):

@@ -297,4 +297,73 @@ LBMRV_HD void relax_node_geier(float g[9], float ux, float uy, const Rates& s,
     g[0] -= h_xxyy - (r_xx + r_yy);
 }
 
+// The same relaxation on one node (R = F1) or two nodes at once (R = F2, one per lane,
+// packed FP32 instructions), with every fused multiply-add written out; UM = UM_FLUID takes
+// u~ = q / rho of the node being relaxed (ux, uy ignored), UM = UM_ZERO skips the shift.
+template <int UM, int RCP, typename R>
+LBMRV_HD void relax_node_geier_r(R g[9], R ux, R uy, const Rates& s, const StoreRef& ref) {
+    const R a = g[5] - g[7], b = g[6] - g[8];
+    const R dsum = (g[5] + g[6]) + (g[7] + g[8]);
+    const R drho = ((g[0] + (g[1] + g[2])) + (g[3] + g[4])) + dsum;
+    const R mjx = (g[1] - g[3]) + (a - b), mjy = (g[2] - g[4]) + (a + b);
+    const R ir = recip<RCP>(R(ref.rho) + drho);
+    const R jx = R(ref.jx) + mjx, jy = R(ref.jy) + mjy;
+    const R vx = jx * ir, vy = jy * ir;  // fluid velocity (equilibrium)
+    if constexpr (UM == UM_FLUID) {
+        ux = vx;
+        uy = vy;
+    }
+    const R third = R(1.0f / 3.0f);
+    const R kx = jx * vx, ky = jy * vy;  // jx^2 / rho, jy^2 / rho
+    // d = m(0) - m_eq(0) on the monomials, product equilibrium (see relax_node_geier)
+    const R d_xx = (((g[1] + g[3]) + dsum) + R(ref.c[0])) - fma_(third, drho, kx);
+    const R d_yy = (((g[2] + g[4]) + dsum) + R(ref.c[1])) - fma_(third, drho, ky);
+    const R pxy = jx * vy;               // jx jy / rho
+    const R d_xy = (((g[5] + g[7]) - (g[6] + g[8])) + R(ref.c[2])) - pxy;
+    const R d_xyy = ((a - b) + R(ref.c[3])) - fma_(third, mjx, pxy * vy);
+    const R d_yxx = ((a + b) + R(ref.c[4])) - fma_(third, mjy, pxy * vx);
+    const R d_xxyy = (dsum + R(ref.c[5])) -
+                     fma_(R(1.0f / 9.0f), drho, fma_(third, kx + ky, kx * (vy * vy)));
+    R k_xyy = d_xyy, k_yxx = d_yxx, k_xxyy = d_xxyy;
+    R ux2 = R(0.0f), uy2 = R(0.0f), uxx = R(0.0f), uyy = R(0.0f), uxy4 = R(0.0f);
+    if constexpr (UM != UM_ZERO) {  // shift to the frame moving at u~
+        ux2 = ux + ux;
+        uy2 = uy + uy;
+        uxx = ux * ux;
+        uyy = uy * uy;
+        uxy4 = ux2 * uy2;
+        k_xyy = d_xyy - fma_(uy2, d_xy, ux * d_yy);
+        k_yxx = d_yxx - fma_(ux2, d_xy, uy * d_xx);
+        k_xxyy = fma_(uyy, d_xx, fma_(uxx, d_yy, fma_(uxy4, d_xy, d_xxyy))) -
+                 fma_(uy2, d_yxx, ux2 * d_xyy);
+    }
+    // relaxation, diagonal in X^2+Y^2, X^2-Y^2, XY, XY^2, X^2Y, X^2Y^2
+    const R half = R(0.5f);
+    const R rt = R(s.e) * (d_xx + d_yy), rd = R(s.pxx) * (d_xx - d_yy);
+    const R r_xx = half * (rt + rd), r_yy = half * (rt - rd);
+    const R r_xy = R(s.pxy) * d_xy;
+    const R r_xyy = R(s.qx) * k_xyy, r_yxx = R(s.qy) * k_yxx, r_xxyy = R(s.eps) * k_xxyy;
+    R h_xyy = r_xyy, h_yxx = r_yxx, h_xxyy = r_xxyy;
+    if constexpr (UM != UM_ZERO) {  // back to the fixed frame
+        h_xyy = fma_(uy2, r_xy, fma_(ux, r_yy, r_xyy));
+        h_yxx = fma_(ux2, r_xy, fma_(uy, r_xx, r_yxx));
+        h_xxyy = fma_(uy2, r_yxx, fma_(ux2, r_xyy,
+                 fma_(uyy, r_xx, fma_(uxx, r_yy, fma_(uxy4, r_xy, r_xxyy)))));
+    }
+    // populations of the increment (monomial moments with zero conserved part)
+    const R mq = R(-0.25f);
+    const R pd = h_xxyy + r_xy, qd = h_xxyy - r_xy;
+    const R r1 = h_xyy + h_yxx, r2 = h_xyy - h_yxx;
+    g[5] = fma_(mq, pd + r1, g[5]);
+    g[7] = fma_(mq, pd - r1, g[7]);
+    g[8] = fma_(mq, qd + r2, g[8]);
+    g[6] = fma_(mq, qd - r2, g[6]);
+    const R ax = r_xx - h_xxyy, ay = r_yy - h_xxyy;
+    g[1] = fma_(R(-0.5f), ax - h_xyy, g[1]);
+    g[3] = fma_(R(-0.5f), ax + h_xyy, g[3]);
+    g[2] = fma_(R(-0.5f), ay - h_yxx, g[2]);
+    g[4] = fma_(R(-0.5f), ay + h_yxx, g[4]);
+    g[0] = g[0] - (h_xxyy - (r_xx + r_yy));
+}
+
 }  // namespace lbmrv

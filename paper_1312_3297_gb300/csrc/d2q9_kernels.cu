@@ -29,6 +29,16 @@ __device__ __forceinline__ void relax_basis(float g[9], float ux, float uy, cons
         relax_node_geier(g, ux, uy, s, ref);
 }
 
+// Two nodes per call (R = F2) for the 8-node packs of 16-bit storage.
+template <int BASIS, int UM, int RCP>
+__device__ __forceinline__ void relax_basis2(F2 g[9], F2 ux, F2 uy, const Rates& s,
+                                             const StoreRef& ref) {
+    if constexpr (BASIS == 0)
+        relax_node<UM, RCP>(g, ux, uy, s, ref);
+    else
+        relax_node_geier_r<UM, RCP>(g, ux, uy, s, ref);
+}
+
 template <int BASIS, int UM>
 constexpr bool needs_utilde() {
     return BASIS != 0 || UM == UM_ANALYTIC || UM == UM_FIELD;
@@ -120,8 +130,17 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 // the storage type) in the block's slot part[4 * block] (sum g, sum c_x g, sum c_y g,
 // non-finite nodes), as k_conserved_partial does for a stored state; k_conserved_final then
 // adds the slots in a fixed order.
+// The paired cascaded relaxation (Geier's basis, 8-node packs) is held to five blocks per
+// SM (96 registers, a few spilled), four with a stored u~ field: with the registers left to
+// the compiler it takes 126, runs four blocks and, for u~ = q / rho, reaches 0.88 of copy
+// bandwidth instead of 0.98 (measured at 8192^2; the stored field runs faster with four).
+// A minimum of 0 blocks leaves every other instance's register budget as without one (same
+// allocation); a minimum of 1 lets the orthogonal-basis 8-node packs grow to 194 registers.
+template <int BASIS, int NV, int UM>
+constexpr int step_vec_min_blocks = (BASIS == 1 && NV >= 8) ? (UM == UM_FIELD ? 4 : 5) : 0;
+
 template <typename T, int NV, int UM, int BASIS, bool SUMS = false>
-__global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
+__global__ void __launch_bounds__(128, (step_vec_min_blocks<BASIS, NV, UM>)) k_step_vec(const T* __restrict__ src,
                                                   T* __restrict__ dst, StepArgs a,
                                                   double* __restrict__ part) {
     pdl_wait_prior();
@@ -144,7 +163,7 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                 ux_row = a.amp_t * cospif(a.two_over_ny * (float)(y + a.y_off));
                 load_pack<float, NV>(a.sin_x + p.x0, true, sx);
             }
-            if constexpr (BASIS == 0 && NV >= 8) {
+            if constexpr (NV >= 8) {
                 // Two nodes per packed FP32 instruction. With 8-node packs (16-bit storage)
                 // the step is issue-bound and pairing removes about a third of its
                 // instructions; with 4 or fewer nodes per thread the broadcast constants'
@@ -163,7 +182,7 @@ __global__ void __launch_bounds__(128) k_step_vec(const T* __restrict__ src,
                         ux = F2(a.amp_t) * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
                         uy = F2(a.amp_t) * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
                     }
-                    relax_node<UM, paired_rcp<UM>()>(h, ux, uy, a.s, a.ref);
+                    relax_basis2<BASIS, UM, paired_rcp<UM>()>(h, ux, uy, a.s, a.ref);
 #pragma unroll
                     for (int j = 0; j < 9; ++j) unpack2(h[j], g[j][k], g[j][k + 1]);
                 }
