@@ -194,7 +194,7 @@ def kernel_label(lattice: str, storage: str, nx: int, mode: str) -> str:
     elif storage == "fp32":
         name = "k_step3"
     else:
-        name = {8: "k_step3_pipe", 4: "k_step3_r16"}.get(nv, "k_step3")
+        name = {8: "k_step3_pipe", 4: "k_step3_pipe_pairs"}.get(nv, "k_step3")
     return f"{name}<{storage},{nv},{mode}>"
 
 

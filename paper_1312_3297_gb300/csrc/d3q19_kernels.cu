@@ -207,80 +207,6 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
                                      blockIdx.x));
 }
 
-// The same step for 16-bit storage with the packs held in storage form (two values per
-// register): wider packs (fewer, larger memory accesses and less per-node address and halo
-// work) at the register cost of narrow ones. Each node pair is converted to FP32 just
-// before it is relaxed by packed FP32 instructions (F2), as an increment added to the pair
-// held in its packed word (measured faster than relaxing node by node or pair by pair in
-// scalar form). Registers are capped at 128 per thread (four 128-thread blocks per SM).
-// Blocks span several rows when a row has fewer than 128 packs (a warp stays within one
-// row); with the row index per thread the compiler spills less than with one row per
-// block (measured).
-template <typename T, int NV, int UM, int RCP>
-__global__ void __launch_bounds__(kThreads3, 4) k_step3_r16(const T* __restrict__ src,
-                                                         T* __restrict__ dst, StepArgs3 a,
-                                                         double* /* no sums */) {
-    pdl_wait_prior();
-    pdl_allow_next();
-    static_assert(sizeof(T) == 2 && NV >= 4 && NV % 2 == 0, "16-bit packs of 4 or more");
-    const int nx = a.nx, ny = a.ny, nz = a.nz;
-    const int64_t n = (int64_t)nx * ny * nz;
-    const PackLane p = pack_lane<NV>(nx);
-    for (int z = blockIdx.z; z < nz; z += gridDim.z) {
-        for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < ny; y += gridDim.y * blockDim.y) {
-            const Rows3 r(y, z, nx, ny, nz);
-            uint32_t w[19][NV / 2];
-            const T* s = src;
-            load_raw16<NV>(s + r.r00 + p.x0, p.act, w[0]);
-            load_raw16_from_left<T, NV>(s + 1 * n + r.r00, p.x0, p.xprev, p.act, p.left_edge, w[1]);
-            load_raw16_from_right<T, NV>(s + 2 * n + r.r00, p.x0, p.xnext, p.act, p.right_edge, w[2]);
-            load_raw16<NV>(s + 3 * n + r.rm0 + p.x0, p.act, w[3]);
-            load_raw16<NV>(s + 4 * n + r.rp0 + p.x0, p.act, w[4]);
-            load_raw16<NV>(s + 5 * n + r.r0m + p.x0, p.act, w[5]);
-            load_raw16<NV>(s + 6 * n + r.r0p + p.x0, p.act, w[6]);
-            load_raw16_from_left<T, NV>(s + 7 * n + r.rm0, p.x0, p.xprev, p.act, p.left_edge, w[7]);
-            load_raw16_from_right<T, NV>(s + 8 * n + r.rp0, p.x0, p.xnext, p.act, p.right_edge, w[8]);
-            load_raw16_from_left<T, NV>(s + 9 * n + r.rp0, p.x0, p.xprev, p.act, p.left_edge, w[9]);
-            load_raw16_from_right<T, NV>(s + 10 * n + r.rm0, p.x0, p.xnext, p.act, p.right_edge, w[10]);
-            load_raw16_from_left<T, NV>(s + 11 * n + r.r0m, p.x0, p.xprev, p.act, p.left_edge, w[11]);
-            load_raw16_from_right<T, NV>(s + 12 * n + r.r0p, p.x0, p.xnext, p.act, p.right_edge, w[12]);
-            load_raw16_from_left<T, NV>(s + 13 * n + r.r0p, p.x0, p.xprev, p.act, p.left_edge, w[13]);
-            load_raw16_from_right<T, NV>(s + 14 * n + r.r0m, p.x0, p.xnext, p.act, p.right_edge, w[14]);
-            load_raw16<NV>(s + 15 * n + r.rmm + p.x0, p.act, w[15]);
-            load_raw16<NV>(s + 16 * n + r.rpp + p.x0, p.act, w[16]);
-            load_raw16<NV>(s + 17 * n + r.rmp + p.x0, p.act, w[17]);
-            load_raw16<NV>(s + 18 * n + r.rpm + p.x0, p.act, w[18]);
-            if (p.act) {
-#pragma unroll
-                for (int k = 0; k < NV / 2; ++k) {
-                    const int64_t i = r.r00 + p.x0 + 2 * k;  // first node of the pair
-                    F2 h[19];
-#pragma unroll
-                    for (int j = 0; j < 19; ++j) {
-                        const float2 f = Cvt16<T>::unpack(w[j][k]);
-                        h[j] = pack2(f.x, f.y);
-                    }
-                    F2 ux(0.0f), uy(0.0f), uz(0.0f);
-                    if constexpr (UM != UM_ZERO && UM != UM_FLUID) {
-                        const F2 amp(a.amp_t);
-                        ux = amp * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
-                        uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
-                        uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
-                    }
-                    relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
-#pragma unroll
-                    for (int j = 0; j < 19; ++j)  // the stored pair plus its increments
-                        w[j][k] = add_to_pair<T>(w[j][k], h[j]);
-                }
-            }
-            if (p.act) {
-#pragma unroll
-                for (int j = 0; j < 19; ++j) store_raw16<NV>(dst + j * n + r.r00 + p.x0, w[j]);
-            }
-        }
-    }
-}
-
 // ---------------------------------------------------------------------------------------
 // 16-bit D3Q19 step with the next row staged in shared memory. Each warp owns a sequence of
 // row segments of 256 nodes (32 lanes x 8-node packs); while it relaxes one, asynchronous
@@ -505,8 +431,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
                     uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
                     uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
                 }
-                // the same arithmetic as k_step3_r16 (increments added to the stored pair),
-                // so that both kernels give the same bits
+                // the same arithmetic as k_step3_pipe_pairs (increments added to the
+                // stored pair), so that both kernels give the same bits
                 relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
 #pragma unroll
                 for (int j = 0; j < 19; ++j) w[j][k] = add_to_pair<T>(w[j][k], h[j]);
@@ -544,6 +470,150 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
         stage = stage == S - 1 ? 0 : stage + 1;
     }
     if constexpr (SUMS) block_sum5(sums, part + 8 * (int64_t)blockIdx.x);
+}
+
+// ---------------------------------------------------------------------------------------
+// 16-bit D3Q19 step for rows of 4-node packs (nx a multiple of 4, not of 8), staged in
+// shared memory with lanes interleaved by node pair. A warp owns a sequence of row
+// segments of 128 nodes; their 19 plane segments arrive by cp.async (lane l copies nodes
+// [4 l, 4 l + 4) of each) into a two-stage ring while the warp relaxes the previous
+// segment. Lane l relaxes the node pairs 2 l and 2 l + 64: it reads each pair's word from
+// shared memory just before relaxing it (the x-moving planes by a byte permute of two
+// neighbouring words, conflict-free across the warp) and stores the relaxed pair straight
+// to global memory, where the warp's 32 words fill one 128-byte line. The arithmetic is
+// that of k_step3_pipe (increments added to the stored pair), so that both give the same
+// bits. Measured on GB300 at 256^3 with 4-node packs, of copy bandwidth: FP16 / BF16 0.847 /
+// 0.842 with u~ = q/rho, against 0.72 / 0.73 for 4-node packs held in registers (16 warps
+// per SM at 128 registers). With 8-node packs (256-node segments, 8-10 warps per SM) it
+// was slower than k_step3_pipe: 0.76-0.86 against 0.92-0.97, at 12 % more instructions
+// per node (the per-pair stores and shared loads) and a lower issue rate.
+// Shared layout of one plane segment, in 32-bit words: word 3 the word left of the segment
+// (planes pulling from x - 1), words 4 .. 3 + nv / 2 the nv nodes of the segment, word
+// 4 + nv / 2 the word right of it (planes pulling from x + 1); periodic in x.
+struct PipePairs {
+    static constexpr int kNpl = 4;                       // nodes per lane and segment
+    static constexpr int kSeg = 32 * kNpl;               // nodes per row segment
+    static constexpr int kPlaneWords = kSeg / 2 + 8;     // head, segment, right word, pad
+    static constexpr int kStageWords = 19 * kPlaneWords;
+    static constexpr int kWarps = 8;                     // per block
+    static constexpr int kBlocksPerSm = 2;
+    static constexpr int kStages = 2;
+    static constexpr int kSmem = kWarps * kStages * kStageWords * 4;  // bytes per block
+};
+
+template <typename T, int UM, int RCP>
+__global__ void __launch_bounds__(PipePairs::kWarps * 32, PipePairs::kBlocksPerSm)
+    k_step3_pipe_pairs(const T* __restrict__ src, T* __restrict__ dst, StepArgs3 a) {
+    using C = PipePairs;
+    constexpr int S = C::kStages, P = C::kNpl / 2, PW = C::kPlaneWords, SEG = C::kSeg;
+    static_assert(sizeof(T) == 2, "16-bit storage");
+    pdl_wait_prior();
+    pdl_allow_next();
+    extern __shared__ __align__(16) uint32_t pairs_smem[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nx = a.nx, ny = a.ny, nz = a.nz;
+    const int64_t n = (int64_t)nx * ny * nz;
+    const int segs = (nx + SEG - 1) / SEG;
+    uint32_t* wbuf = pairs_smem + warp * S * C::kStageWords;
+
+    // Warp w takes work items (row segments, x fastest, then y, z) w, w + W, w + 2W, ...
+    // (W warps in the grid); a cursor (seg, y, z) steps by W in mixed radix (segs, ny, nz).
+    const int64_t nwarps = (int64_t)gridDim.x * C::kWarps;
+    struct Cursor {
+        int seg, y, z;
+    };
+    auto split = [&](int64_t it) {
+        const int64_t row = it / segs;
+        Cursor c;
+        c.seg = (int)(it - row * segs);
+        c.z = (int)(row / ny);
+        c.y = (int)(row - (int64_t)c.z * ny);
+        return c;
+    };
+    const Cursor step = split(nwarps);
+    auto advance = [&](Cursor c) {
+        c.seg += step.seg;
+        int carry = c.seg >= segs;
+        c.seg -= carry ? segs : 0;
+        c.y += step.y + carry;
+        carry = c.y >= ny;
+        c.y -= carry ? ny : 0;
+        c.z += step.z + carry;
+        return c;
+    };
+    // queue the copies of the item at `c` into buffer `stg`
+    auto copy = [&](const Cursor& c, int stg) {
+        if (c.z < nz) {
+            const RowNums3 r(c.y, c.z, ny, nz);
+            uint32_t* sb = wbuf + stg * C::kStageWords;
+            const int xs = c.seg * SEG;
+            const int nv = nx - xs < SEG ? nx - xs : SEG;  // nodes in this segment
+            const int xl = xs + lane * C::kNpl;             // this lane's copy
+            const int x_left = (xs == 0 ? nx : xs) - 2;     // word left of the segment
+            const int x_right = xs + nv == nx ? 0 : xs + nv;  // word right of it
+#pragma unroll
+            for (int j = 0; j < 19; ++j) {
+                const T* row = src + j * n + (int64_t)plane_rownum(r, j) * nx;
+                uint32_t* pl = sb + j * PW;
+                if (xl < nx) cp_async8(pl + 4 + lane * 2, row + xl);
+                if (lane == 0 && plane_shift(j) == 1) cp_async4(pl + 3, row + x_left);
+                if (lane == 0 && plane_shift(j) == 2) cp_async4(pl + 4 + nv / 2, row + x_right);
+            }
+        }
+    };
+
+    Cursor cur = split((int64_t)blockIdx.x * C::kWarps + warp), ahead = cur;
+#pragma unroll
+    for (int s = 0; s < S - 1; ++s) {
+        copy(ahead, s);
+        cp_async_commit();
+        ahead = advance(ahead);
+    }
+    int stage = 0, fill = S - 1;
+    while (cur.z < nz) {
+        copy(ahead, fill);
+        cp_async_commit();
+        cp_async_wait_all_but<S - 1>();  // the oldest group: the item at `cur`
+        __syncwarp();                    // the other lanes' copies are visible
+        const uint32_t* sb = wbuf + stage * C::kStageWords;
+        const int xs = cur.seg * SEG;
+        const int nv = nx - xs < SEG ? nx - xs : SEG;
+        const int64_t r0 = (int64_t)(cur.z * ny + cur.y) * nx + xs;  // first node
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const int q = lane + 32 * k;  // node pair of the segment
+            if (2 * q < nv) {
+                uint32_t w[19];
+                F2 h[19];
+#pragma unroll
+                for (int j = 0; j < 19; ++j) {
+                    const uint32_t* pl = sb + j * PW + 4 + q;
+                    w[j] = plane_shift(j) == 1 ? __byte_perm(pl[-1], pl[0], 0x5432)
+                         : plane_shift(j) == 2 ? __byte_perm(pl[0], pl[1], 0x5432)
+                                               : pl[0];
+                    const float2 f = Cvt16<T>::unpack(w[j]);
+                    h[j] = pack2(f.x, f.y);
+                }
+                const int64_t i = r0 + 2 * q;  // first node of the pair
+                F2 ux(0.0f), uy(0.0f), uz(0.0f);
+                if constexpr (UM != UM_ZERO && UM != UM_FLUID) {
+                    const F2 amp(a.amp_t);
+                    ux = amp * pack2(__ldg(a.ut0 + i), __ldg(a.ut0 + i + 1));
+                    uy = amp * pack2(__ldg(a.ut0 + n + i), __ldg(a.ut0 + n + i + 1));
+                    uz = amp * pack2(__ldg(a.ut0 + 2 * n + i), __ldg(a.ut0 + 2 * n + i + 1));
+                }
+                relax_node3<UM, RCP, true>(h, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                for (int j = 0; j < 19; ++j)
+                    *reinterpret_cast<uint32_t*>(dst + j * n + i) = add_to_pair<T>(w[j], h[j]);
+            }
+        }
+        __syncwarp();  // every lane is done with `stage` before it is refilled
+        ahead = advance(ahead);
+        fill = fill == S - 1 ? 0 : fill + 1;
+        cur = advance(cur);
+        stage = stage == S - 1 ? 0 : stage + 1;
+    }
 }
 
 __constant__ int kC3X[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -695,57 +765,87 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 }
 
 // 16-bit packs of 4 and 8 nodes run in storage form, relaxed in pairs by packed FP32
-// instructions, with the correctly rounded 1/rho (measured fastest on GB300 at 256^3).
-// 8-node packs run the shared-memory pipeline (k_step3_pipe) unless ny * nz needs more
-// than 31 bits; then, and for 4-node packs, the register kernel (k_step3_r16) runs 4-node
-// packs.
+// instructions, with the correctly rounded 1/rho (measured fastest on GB300 at 256^3), by
+// the shared-memory pipelines: 8-node packs by k_step3_pipe, 4-node packs by
+// k_step3_pipe_pairs. Both number rows in 32 bits (ny * nz < 2^31, which any 16-bit
+// lattice of 4 or more nodes per row that fits in device memory meets); beyond that
+// 2-node packs run.
 constexpr int kRcp3 = RCP_RN;
+constexpr int kMaxDevices3 = 64;
+
+// Resident blocks of a persistent kernel on the current device (SMs x blocks per SM, at
+// most max_per_sm), found once per device with the shared-memory attribute set and kept
+// in cache[device] (0 = not yet known).
+template <typename... KArgs>
+cudaError_t resident_blocks(void (*kernel)(KArgs...), std::atomic<int>* cache, int threads,
+                            int smem, int max_per_sm, int* full) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    *full = dev < kMaxDevices3 ? cache[dev].load(std::memory_order_relaxed) : 0;
+    if (*full != 0) return cudaSuccess;
+    int sms = 0, per_sm = 0;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = per_sm < 1 ? 1 : (per_sm > max_per_sm ? max_per_sm : per_sm);
+    *full = per_sm * sms;
+    if (dev < kMaxDevices3) cache[dev].store(*full, std::memory_order_relaxed);
+    return cudaSuccess;
+}
+
+// Blocks of a persistent pipeline over the lattice's row segments: no more than are
+// resident at once (work is split between warps up front), no more than there is work.
+inline int pipeline_blocks(const StepArgs3& a, int seg, int warps, int full) {
+    const int64_t segs = (a.nx + seg - 1) / seg;
+    const int64_t items = (int64_t)a.ny * a.nz * segs;
+    const int64_t need = (items + warps - 1) / warps;
+    return (int)(need < full ? need : full);
+}
 
 template <typename T, int UM, bool SUMS = false>
 cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
                          double* part = nullptr, int64_t* slots = nullptr) {
     auto kernel = k_step3_pipe<T, UM, kRcp3, SUMS>;
-    // Resident blocks of this kernel on each device (SMs x blocks per SM), found once per
-    // device with the shared-memory attribute set: 0 = not yet known.
-    constexpr int kMaxDevices = 64;
-    static std::atomic<int> resident[kMaxDevices];
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static std::atomic<int> resident[kMaxDevices3];
+    int full = 0;
+    cudaError_t e = resident_blocks(kernel, resident, kPipeWarps * 32, kPipeSmem,
+                                    kPipeBlocksPerSm, &full);
     if (e != cudaSuccess) return e;
-    int full = dev < kMaxDevices ? resident[dev].load(std::memory_order_relaxed) : 0;
-    if (full == 0) {
-        int sms = 0, per_sm = 0;
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kPipeSmem);
-        if (e == cudaSuccess)
-            e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel,
-                                                              kPipeWarps * 32, kPipeSmem);
-        if (e != cudaSuccess) return e;
-        // persistent: no more blocks than are resident at once (work is split between
-        // warps up front)
-        per_sm = per_sm < 1 ? 1 : (per_sm > kPipeBlocksPerSm ? kPipeBlocksPerSm : per_sm);
-        full = per_sm * sms;
-        if (dev < kMaxDevices) resident[dev].store(full, std::memory_order_relaxed);
-    }
-    const int64_t segs = (a.nx + kPipeSeg - 1) / kPipeSeg;
-    const int64_t items = (int64_t)a.ny * a.nz * segs;
-    const int64_t need = (items + kPipeWarps - 1) / kPipeWarps;
-    const int blocks = (int)(need < full ? need : full);
+    const int blocks = pipeline_blocks(a, kPipeSeg, kPipeWarps, full);
     if (slots) *slots = blocks;
     e = launch_pdl_smem(kernel, dim3(blocks), dim3(kPipeWarps * 32), kPipeSmem, st,
                         static_cast<const T*>(src), static_cast<T*>(dst), a, part);
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+template <typename T, int UM>
+cudaError_t launch_pipe_pairs(const void* src, void* dst, const StepArgs3& a,
+                              cudaStream_t st) {
+    using C = PipePairs;
+    auto kernel = k_step3_pipe_pairs<T, UM, kRcp3>;
+    static std::atomic<int> resident[kMaxDevices3];
+    int full = 0;
+    cudaError_t e = resident_blocks(kernel, resident, C::kWarps * 32, C::kSmem,
+                                    C::kBlocksPerSm, &full);
+    if (e != cudaSuccess) return e;
+    const int blocks = pipeline_blocks(a, C::kSeg, C::kWarps, full);
+    e = launch_pdl_smem(kernel, dim3(blocks), dim3(C::kWarps * 32), C::kSmem, st,
+                        static_cast<const T*>(src), static_cast<T*>(dst), a);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+inline bool rows_fit_31_bits(const StepArgs3& a) { return (int64_t)a.ny * a.nz < (1LL << 31); }
+
 // The step with the conserved sums fused in: the FP32 4-node kernel or the 16-bit
-// pipeline; *slots receives the number of block slots written.
+// 8-node pipeline; *slots receives the number of block slots written.
 template <typename T, int UM>
 cudaError_t step3_sums(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
                        int nv, double* part, int64_t* slots) {
     if constexpr (sizeof(T) == 2) {
-        if (nv == 8 && (int64_t)a.ny * a.nz < (1LL << 31))
+        if (nv == 8 && rows_fit_31_bits(a))
             return launch_pipe3<T, UM, true>(src, dst, a, st, part, slots);
     } else {
         if (nv == 4) {
@@ -760,10 +860,9 @@ cudaError_t step3_sums(const void* src, void* dst, const StepArgs3& a, cudaStrea
 template <typename T, int UM>
 cudaError_t step3_nv(const void* src, void* dst, const StepArgs3& a, cudaStream_t st, int nv) {
     if constexpr (sizeof(T) == 2) {
-        if (nv == 8 && (int64_t)a.ny * a.nz < (1LL << 31))
-            return launch_pipe3<T, UM>(src, dst, a, st);
-        if (nv == 4 || nv == 8)  // (8-node packs with ny * nz >= 2^31: 4-node packs)
-            return launch3(k_step3_r16<T, 4, UM, kRcp3>, src, dst, a, st, 4, true);
+        if (nv == 8 && rows_fit_31_bits(a)) return launch_pipe3<T, UM>(src, dst, a, st);
+        if (nv == 4 && rows_fit_31_bits(a)) return launch_pipe_pairs<T, UM>(src, dst, a, st);
+        if (nv == 4 || nv == 8) nv = 2;
     } else {
         if (nv == 4) return launch3(k_step3<T, 4, UM>, src, dst, a, st, nv);
     }
