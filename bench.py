@@ -4,7 +4,8 @@ Headline workload: D2Q9 FP32, 4096 x 4096 periodic, Taylor-Green vortex u0 = 0.0
 rho0 = 1, s = (0,0,0,1.4,1.8,1.8,1.2,1.2,1.4) (s_nu = 1.8), prescribed relative velocity
 u~(x,t) = 0.03 (cos 2 pi y/L, sin 2 pi x/L) cos(2 pi t / 1000). One bench step is one
 time step (pull transport + relaxation in the moving frame), one kernel launch. The
-1.2 GB state is larger than L2, so no flush is needed between steps.
+0.6 GB state (1.2 GB moved per step) is larger than L2, so no flush is needed between
+steps.
 
 ``python bench.py [--gpus N] [--steps K] [--warmup W]`` prints one JSON line.
 ``--impl reference`` times the FP64 CPU oracle on the host cores instead (same metric).
@@ -186,11 +187,11 @@ def default_width(lattice: str, storage: str, nx: int) -> int:
     return widest
 
 
-def kernel_label(lattice: str, storage: str, nx: int, mode: str) -> str:
+def kernel_label(lattice: str, storage: str, nx: int, mode: str, scheme: str = "rv") -> str:
     """Name of the step kernel the library launches for this configuration."""
     nv = default_width(lattice, storage, nx)
     if lattice == "d2q9":
-        name = "k_step_vec"
+        name = "k_step_vec" if scheme == "rv" else "k_step_vec, Geier basis"
     elif storage == "fp32":
         name = "k_step3"
     else:
@@ -307,7 +308,11 @@ def gpu_arm(args):
     else:
         n = size * size
         fields = inp.taylor_green(size, size, u0=0.04)
-        sim = make_sim(torch, D2Q9, inp, args.storage, args.mode, size, fields)
+        if args.scheme == "cascaded":
+            from paper_1312_3297_gb300 import D2Q9Cascaded as scheme
+        else:
+            scheme = D2Q9
+        sim = make_sim(torch, scheme, inp, args.storage, args.mode, size, fields)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
@@ -342,7 +347,7 @@ def gpu_arm(args):
     mlups = job_mlups(n, world, args.steps, ms)
     e2e = None
     if not args.no_e2e and size == L and args.storage == "fp32" and args.mode == "prescribed" \
-            and args.lattice == "d2q9" and args.decomp == "replicas":
+            and args.lattice == "d2q9" and args.decomp == "replicas" and args.scheme == "rv":
         # every rank runs its replica end to end; the job's figure takes the slowest rank
         if world > 1:
             dist.barrier()
@@ -353,7 +358,8 @@ def gpu_arm(args):
     bpn = BYTES_PER_NODE[args.storage] * (19 / 9 if args.lattice == "d3q19" else 1)
     achieved = bpn * n / (per_step_ms * 1e-3) / 1e9
     headline = (size == L and args.storage == "fp32" and args.mode == "prescribed"
-                and args.lattice == "d2q9" and args.decomp == "replicas")
+                and args.lattice == "d2q9" and args.decomp == "replicas"
+                and args.scheme == "rv")
     out = None
     if rank == 0:
         extras = {}
@@ -399,16 +405,18 @@ def gpu_arm(args):
             "dtype": "f32" if args.storage == "fp32" else f"{args.storage} storage, f32 math",
             "data": "synthetic",
             "config": {"workload": WORKLOAD if headline else
-                       f"{args.lattice} {args.storage} side {size} Taylor-Green, u~ mode {args.mode}",
+                       f"{args.lattice}{' cascaded' if args.scheme == 'cascaded' else ''} "
+                       f"{args.storage} side {size} Taylor-Green, u~ mode {args.mode}",
                        "nodes": n, "bytes_per_node_step": round(bpn, 1),
-                       "l2": "state 1.2 GB > 129 MB L2; no flush needed",
+                       "l2": f"state {bpn / 2 * n / 1e9:.2f} GB > 129 MB L2; no flush needed",
                        "parallelism": f"{args.decomp} x{world}"},
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": recorded_traffic() if headline else None,
                          "peak_kind": peak_kind,
                          "frac_of_nominal_7900": round(achieved / 7900.0, 4),
-                         "kernel": kernel_label(args.lattice, args.storage, size, args.mode)},
+                         "kernel": kernel_label(args.lattice, args.storage, size, args.mode,
+                                                args.scheme)},
             "clocks": clock_info,
             "e2e": e2e,
             # one step kernel per step and rank; a slab adds its pack and unpack kernels
@@ -842,6 +850,9 @@ def main():
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
                     help="N > 1: independent replicas (default), or one lattice of N stacked "
                          "Taylor-Green cells split into slabs with a halo exchange per step")
+    ap.add_argument("--scheme", default="rv", choices=["rv", "cascaded"],
+                    help="D2Q9 relaxation of the timed run: the relative-velocity scheme's "
+                         "orthogonal basis (rv) or Geier's cascaded basis (profiling captures)")
     ap.add_argument("--case", default="step", choices=["step", "adjoint"],
                     help="adjoint: only the adjoint workload's timings (profiling captures)")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
