@@ -765,12 +765,19 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 }
 
 // 16-bit packs of 4 and 8 nodes run in storage form, relaxed in pairs by packed FP32
-// instructions, with the correctly rounded 1/rho (measured fastest on GB300 at 256^3), by
-// the shared-memory pipelines: 8-node packs by k_step3_pipe, 4-node packs by
+// instructions, by the shared-memory pipelines: 8-node packs by k_step3_pipe, 4-node packs by
 // k_step3_pipe_pairs. Both number rows in 32 bits (ny * nz < 2^31, which any 16-bit
 // lattice of 4 or more nodes per row that fits in device memory meets); beyond that
 // 2-node packs run.
-constexpr int kRcp3 = RCP_RN;
+// Form of 1/rho in the 16-bit pipelines, measured on GB300 at 256^3 (8-node packs, of copy
+// bandwidth): FP16 with u~ = q/rho takes the fast division (0.938, against 0.934 with the
+// approximation and 0.921 correctly rounded); the other kernels keep the correctly rounded
+// reciprocal, which the fast division slows to 0.86 (FP16 u~ = 0), 0.72 (BF16 u~ = q/rho)
+// and 0.87 (BF16 u~ = 0). Both pipelines take the same form, so they give the same bits.
+template <typename T, int UM>
+constexpr int rcp3() {
+    return (std::is_same<T, __half>::value && UM == UM_FLUID) ? RCP_DIV : RCP_RN;
+}
 constexpr int kMaxDevices3 = 64;
 
 // Resident blocks of a persistent kernel on the current device (SMs x blocks per SM, at
@@ -808,7 +815,7 @@ inline int pipeline_blocks(const StepArgs3& a, int seg, int warps, int full) {
 template <typename T, int UM, bool SUMS = false>
 cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
                          double* part = nullptr, int64_t* slots = nullptr) {
-    auto kernel = k_step3_pipe<T, UM, kRcp3, SUMS>;
+    auto kernel = k_step3_pipe<T, UM, rcp3<T, UM>(), SUMS>;
     static std::atomic<int> resident[kMaxDevices3];
     int full = 0;
     cudaError_t e = resident_blocks(kernel, resident, kPipeWarps * 32, kPipeSmem,
@@ -825,7 +832,7 @@ template <typename T, int UM>
 cudaError_t launch_pipe_pairs(const void* src, void* dst, const StepArgs3& a,
                               cudaStream_t st) {
     using C = PipePairs;
-    auto kernel = k_step3_pipe_pairs<T, UM, kRcp3>;
+    auto kernel = k_step3_pipe_pairs<T, UM, rcp3<T, UM>()>;
     static std::atomic<int> resident[kMaxDevices3];
     int full = 0;
     cudaError_t e = resident_blocks(kernel, resident, C::kWarps * 32, C::kSmem,
