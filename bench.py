@@ -396,6 +396,8 @@ def gpu_arm(args):
             extras["adjoint_16bit_1024"] = {
                 st: adjoint_step_measure(torch, D2Q9, inp, peak, 1024, 1000, st)
                 for st in ("fp16", "bf16")}
+            extras["adjoint_16bit_4096"] = adjoint_step_measure(torch, D2Q9, inp, peak, 4096,
+                                                                60, "fp16")
             extras["d3q19_256"] = d3q19_measure(torch, inp, k, peak)
         cpu = cpu_baseline_measure() if (world == 1 and not args.no_cpu) else None
         out = {
@@ -467,7 +469,8 @@ def slab_measure(torch, D2Q9, inp, fields, steps, peak, ref_ms):
 def sums_measure(torch, D2Q9, inp, fields, reps: int = 30):
     """One step followed by the FP64 conserved sums of its result, synchronously: with the
     sums fused into the step kernel (lbmrv_step_conserved) and with the separate reduction
-    pass over the stored state (lbmrv_step + lbmrv_conserved3). Wall clock per check."""
+    pass over the stored state (lbmrv_step + lbmrv_conserved3). Wall clock per check, host
+    calls and the read-back included (the kernels' own times: `--case sums` under ncu)."""
     sim = make_sim(torch, D2Q9, inp, "fp32", "prescribed", L, fields)
     sim.step(3)
     out = {}
@@ -484,6 +487,47 @@ def sums_measure(torch, D2Q9, inp, fields, reps: int = 30):
     sim.close()
     out["saved_ms"] = round(out["separate_ms"] - out["fused_ms"], 4)
     return out
+
+
+def sums_arm(args):
+    """The conserved-sum checks alone (profiling captures): on D2Q9 4096^2 (FP32, FP16;
+    prescribed u~) and D3Q19 256^3 (FP32, FP16; u~ = q/rho), three plain steps, then
+    `args.steps` rounds of a fused check (lbmrv_step_conserved) and a separate one
+    (lbmrv_step + lbmrv_conserved3). Prints the median wall clock per check as one JSON
+    line; ncu's launch list of this command gives the kernels' times."""
+    import torch
+
+    import lbm_inputs as inp
+    from paper_1312_3297_gb300 import D2Q9, D3Q19, binding
+
+    binding.load()
+    out = {}
+    fields = inp.taylor_green(L, L, u0=0.04)
+    d3 = inp.taylor_green_3d(256, 256, 256, u0=0.04)
+    s3 = [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3
+    for lattice in ("d2q9", "d3q19"):
+        for st in ("fp32", "fp16"):
+            if lattice == "d2q9":
+                sim = make_sim(torch, D2Q9, inp, st, "prescribed", L, fields)
+            else:
+                sim = D3Q19(256, 256, 256, s3, mode="fluid", storage=st)
+                sim.init_equilibrium(torch.as_tensor(d3["rho"], dtype=torch.float32),
+                                     *(torch.as_tensor(c, dtype=torch.float32)
+                                       for c in d3["u"]))
+            sim.step(3)
+            fused, separate = [], []
+            for _ in range(args.steps):
+                t0 = time.perf_counter()
+                sim.step_conserved(1)
+                fused.append((time.perf_counter() - t0) * 1e3)
+                t0 = time.perf_counter()
+                sim.step(1)
+                sim.conserved3()
+                separate.append((time.perf_counter() - t0) * 1e3)
+            sim.close()
+            out[f"{lattice}_{st}"] = {"fused_ms": round(statistics.median(fused), 4),
+                                      "separate_ms": round(statistics.median(separate), 4)}
+    print(json.dumps({"case": "sums", "checks": args.steps, **out}), flush=True)
 
 
 def cascaded_measure(torch, inp, fields, steps, peak):
@@ -853,8 +897,9 @@ def main():
     ap.add_argument("--scheme", default="rv", choices=["rv", "cascaded"],
                     help="D2Q9 relaxation of the timed run: the relative-velocity scheme's "
                          "orthogonal basis (rv) or Geier's cascaded basis (profiling captures)")
-    ap.add_argument("--case", default="step", choices=["step", "adjoint"],
-                    help="adjoint: only the adjoint workload's timings (profiling captures)")
+    ap.add_argument("--case", default="step", choices=["step", "adjoint", "sums"],
+                    help="adjoint: only the adjoint workload's timings; sums: only the "
+                         "conserved-sum checks (profiling captures)")
     ap.add_argument("--adjoint-steps", type=int, default=2000,
                     help="time steps of the adjoint workload's whole-gradient run")
     args = ap.parse_args()
@@ -864,6 +909,8 @@ def main():
         reference_arm(args)
     elif args.case == "adjoint":
         adjoint_arm(args)
+    elif args.case == "sums":
+        sums_arm(args)
     else:
         gpu_arm(args)
 

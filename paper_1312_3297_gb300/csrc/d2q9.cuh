@@ -10,6 +10,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #ifdef __CUDACC__
 #include "f32x2.cuh"
 #endif
@@ -112,6 +114,17 @@ LBMRV_HD NodeMoments node_moments(const float g[9]) {
 }
 
 LBMRV_HD float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+
+// x is neither infinite nor NaN. On the device an integer test of the exponent bits, so
+// that no FP64 instruction is involved (FP64 issues at 2 operations per clock per SM on
+// this GPU).
+LBMRV_HD bool finite_f(float x) {
+#ifdef __CUDA_ARCH__
+    return (__float_as_uint(x) & 0x7f800000u) != 0x7f800000u;
+#else
+    return std::isfinite(x);
+#endif
+}
 
 #ifdef __CUDACC__
 // Lane-wise reciprocal of a pair of densities.

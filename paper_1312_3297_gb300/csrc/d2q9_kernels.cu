@@ -6,6 +6,7 @@
 
 #include "d2q9.cuh"
 #include "launch.h"
+#include "occupancy.cuh"
 #include "pdl.cuh"
 #include "pull.cuh"
 
@@ -129,27 +130,35 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 // SUMS: also add up the conserved moments of the stored result (the values as rounded to
 // the storage type) in the block's slot part[4 * block] (sum g, sum c_x g, sum c_y g,
 // non-finite nodes), as k_conserved_partial does for a stored state; k_conserved_final then
-// adds the slots in a fixed order.
+// adds the slots in a fixed order. The launcher then sizes the grid to the blocks resident
+// at once, so each block walks many rows and its FP64 reduction runs once.
 // The paired cascaded relaxation (Geier's basis, 8-node packs) is held to five blocks per
 // SM (96 registers, a few spilled), four with a stored u~ field: with the registers left to
 // the compiler it takes 126, runs four blocks and, for u~ = q / rho, reaches 0.88 of copy
 // bandwidth instead of 0.98 (measured at 8192^2; the stored field runs faster with four).
 // A minimum of 0 blocks leaves every other instance's register budget as without one (same
 // allocation); a minimum of 1 lets the orthogonal-basis 8-node packs grow to 194 registers.
-template <int BASIS, int NV, int UM>
-constexpr int step_vec_min_blocks = (BASIS == 1 && NV >= 8) ? (UM == UM_FIELD ? 4 : 5) : 0;
+// The instances with fused sums (not the timed step) keep the compiler's choice.
+template <int BASIS, int NV, int UM, bool SUMS>
+constexpr int step_vec_min_blocks =
+    (BASIS == 1 && NV >= 8 && !SUMS) ? (UM == UM_FIELD ? 4 : 5) : 0;
 
 template <typename T, int NV, int UM, int BASIS, bool SUMS = false>
-__global__ void __launch_bounds__(128, (step_vec_min_blocks<BASIS, NV, UM>)) k_step_vec(const T* __restrict__ src,
-                                                  T* __restrict__ dst, StepArgs a,
-                                                  double* __restrict__ part) {
+__global__ void __launch_bounds__(128, (step_vec_min_blocks<BASIS, NV, UM, SUMS>))
+    k_step_vec(const T* __restrict__ src, T* __restrict__ dst, StepArgs a,
+               double* __restrict__ part) {
     pdl_wait_prior();
     pdl_allow_next();
     const int nx = a.nx, ny = a.ny;
     const int64_t n = (int64_t)nx * ny;
     const PackLane p = pack_lane<NV>(nx);
-    double sums[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int y = blockIdx.y; y < ny; y += gridDim.y) {
+    // SUMS: node moments in FP32 runs of kRun packs (32 nodes), each run added in FP64 (FP64
+    // adds are scarce on this GPU; a run of 32 loses < 1e-6 relative)
+    constexpr int kRun = NV >= 32 ? 1 : 32 / NV;
+    double sums[3] = {0.0, 0.0, 0.0};
+    float run_r[3] = {0.f, 0.f, 0.f};
+    int bad = 0;
+    auto row = [&](int y) {
         const int ym = y == 0 ? ny - 1 : y - 1;
         const int yp = y == ny - 1 ? 0 : y + 1;
         const int64_t r0 = (int64_t)y * nx, rm = (int64_t)ym * nx, rp = (int64_t)yp * nx;
@@ -205,29 +214,53 @@ __global__ void __launch_bounds__(128, (step_vec_min_blocks<BASIS, NV, UM>)) k_s
                 }
             }
 #pragma unroll
-            for (int j = 0; j < 9; ++j) store_pack<T, NV>(dst + j * n + r0 + p.x0, g[j]);
+            for (int j = 0; j < 9; ++j) {
+                if constexpr (SUMS) {  // keep the stored (rounded) values for the sums
+                    Pack<T, NV> pk;
+                    PackCvt<T, NV>::out(g[j], pk);
+                    *reinterpret_cast<Pack<T, NV>*>(dst + j * n + r0 + p.x0) = pk;
+                    PackCvt<T, NV>::in(pk, g[j]);
+                } else {
+                    store_pack<T, NV>(dst + j * n + r0 + p.x0, g[j]);
+                }
+            }
             if constexpr (SUMS) {
-                float r[3] = {0.f, 0.f, 0.f};  // NV <= 8 node moments in FP32, then FP64
-                int bad = 0;
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
                     float h[9];
 #pragma unroll
-                    for (int j = 0; j < 9; ++j) h[j] = to_f(from_f<T>(g[j][k]));
+                    for (int j = 0; j < 9; ++j) h[j] = g[j][k];
                     const NodeMoments m = node_moments(h);
-                    r[0] += m.drho;
-                    r[1] += m.jx;
-                    r[2] += m.jy;
-                    bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy)) ? 0 : 1;
+                    run_r[0] += m.drho;
+                    run_r[1] += m.jx;
+                    run_r[2] += m.jy;
+                    bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy)) ? 0 : 1;
                 }
+            }
+        }
+    };
+    if constexpr (!SUMS) {
+        for (int y = blockIdx.y; y < ny; y += gridDim.y) row(y);
+    } else {
+        // rows in chunks of kRun (one pack per thread and row); a chunk's FP32 run is added
+        // in FP64 after it, outside the rows' loop (FP64 issues at 2 operations per clock
+        // per SM on this GPU, and predicated adds inside the loop would hold that pipe)
+        for (int y0 = blockIdx.y; y0 < ny; y0 += kRun * gridDim.y) {
+            for (int t = 0, y = y0; t < kRun && y < ny; ++t, y += gridDim.y) row(y);
 #pragma unroll
-                for (int c = 0; c < 3; ++c) sums[c] += (double)r[c];
-                sums[3] += (double)bad;
+            for (int c = 0; c < 3; ++c) {
+                sums[c] += (double)run_r[c];
+                run_r[c] = 0.f;
             }
         }
     }
-    if constexpr (SUMS)
-        block_sum4<128>(sums, part + 4 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
+    if constexpr (SUMS) {
+        double v[4];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = sums[c] + (double)run_r[c];
+        v[3] = (double)bad;
+        block_sum4<128>(v, part + 4 * ((int64_t)blockIdx.y * gridDim.x + blockIdx.x));
+    }
 }
 
 // --------------------------------------------------------------------------------------
@@ -311,31 +344,28 @@ __global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* _
                                                                       int64_t n, int64_t plane,
                                                                       double* __restrict__ part) {
     // Node moments are FP32; each thread adds runs of up to 32 of them in FP32 and the
-    // runs in FP64 (FP64 adds are scarce on this GPU; a run of 32 loses < 1e-6 relative).
+    // runs in FP64 (a run of 32 loses < 1e-6 relative). The FP64 adds sit after the run's
+    // loop rather than under a condition inside it: FP64 issues at 2 operations per clock
+    // per SM on this GPU, and a predicated add inside the loop held that pipe every node.
     double v[4] = {0.0, 0.0, 0.0, 0.0};
-    float r[3] = {0.f, 0.f, 0.f};
-    int run = 0, bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float g[9];
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    while (i < n) {
+        float r[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < 32 && i < n; ++k, i += stride) {
+            float g[9];
 #pragma unroll
-        for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * plane + i]);
-        const NodeMoments m = node_moments(g);
-        r[0] += m.drho;
-        r[1] += m.jx;
-        r[2] += m.jy;
-        bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy)) ? 0 : 1;
-        if (++run == 32) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                v[c] += (double)r[c];
-                r[c] = 0.f;
-            }
-            run = 0;
+            for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * plane + i]);
+            const NodeMoments m = node_moments(g);
+            r[0] += m.drho;
+            r[1] += m.jx;
+            r[2] += m.jy;
+            bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy)) ? 0 : 1;
         }
-    }
 #pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] += (double)r[c];
+        for (int c = 0; c < 3; ++c) v[c] += (double)r[c];
+    }
     v[3] = (double)bad;
     block_sum4<kReduceThreads>(v, part + 4 * (int64_t)blockIdx.x);
 }
@@ -395,19 +425,32 @@ __global__ void __launch_bounds__(kReduceThreads) k_sum_partials(const double* _
 }
 
 
+// With the sums (part != nullptr) the grid has as many blocks as are resident at once
+// (rows strided over blocks), and *nblk receives the number of block slots written: with
+// one row per block the FP64 block reductions of a 4096^2 step took longer than the step.
 template <typename T, int NV, int UM, int BASIS>
-cudaError_t launch_vec(const T* s, T* d, const StepArgs& a, cudaStream_t st, double* part) {
-    const dim3 grid(((a.nx / NV) + 127) / 128, a.ny < 65535 ? a.ny : 65535);
+cudaError_t launch_vec(const T* s, T* d, const StepArgs& a, cudaStream_t st, double* part,
+                       int64_t* nblk) {
+    const int gx = ((a.nx / NV) + 127) / 128;
+    const int rows = a.ny < 65535 ? a.ny : 65535;
     // successive steps overlap their launch with the previous step's tail (pdl.cuh)
-    return part ? launch_pdl(k_step_vec<T, NV, UM, BASIS, true>, grid, dim3(128), st, s, d, a,
-                             part)
-                : launch_pdl(k_step_vec<T, NV, UM, BASIS, false>, grid, dim3(128), st, s, d, a,
-                             static_cast<double*>(nullptr));
+    if (!part)
+        return launch_pdl(k_step_vec<T, NV, UM, BASIS, false>, dim3(gx, rows), dim3(128), st, s,
+                          d, a, static_cast<double*>(nullptr));
+    auto kernel = k_step_vec<T, NV, UM, BASIS, true>;
+    static std::atomic<int> resident[kMaxDevicesOcc];
+    int full = 0;
+    const cudaError_t e = resident_blocks(kernel, resident, 128, 0, 32, &full);
+    if (e != cudaSuccess) return e;
+    const int per_x = full / gx;
+    const int gy = per_x < 1 ? 1 : (per_x < rows ? per_x : rows);
+    if (nblk) *nblk = (int64_t)gx * gy;
+    return launch_pdl(kernel, dim3(gx, gy), dim3(128), st, s, d, a, part);
 }
 
 template <typename T, int UM, int BASIS>
 cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
-                             int nv, double* part) {
+                             int nv, double* part, int64_t* nblk) {
     const T* s = static_cast<const T*>(src);
     T* d = static_cast<T*>(dst);
     const int gy = a.ny < 65535 ? a.ny : 65535;
@@ -417,12 +460,12 @@ cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cuda
         e = launch_pdl(k_step_scalar<T, UM, BASIS>, dim3((a.nx + 255) / 256, gy), dim3(256), st,
                        s, d, a);
     } else if (nv == 2) {
-        e = launch_vec<T, 2, UM, BASIS>(s, d, a, st, part);
+        e = launch_vec<T, 2, UM, BASIS>(s, d, a, st, part, nblk);
     } else if (nv == 4) {
-        e = launch_vec<T, 4, UM, BASIS>(s, d, a, st, part);
+        e = launch_vec<T, 4, UM, BASIS>(s, d, a, st, part, nblk);
     } else if (nv == 8) {
         if constexpr (sizeof(T) == 2) {
-            e = launch_vec<T, 8, UM, BASIS>(s, d, a, st, part);
+            e = launch_vec<T, 8, UM, BASIS>(s, d, a, st, part, nblk);
         } else {
             return cudaErrorInvalidValue;
         }
@@ -434,22 +477,25 @@ cudaError_t step_dispatch_nv(const void* src, void* dst, const StepArgs& a, cuda
 
 template <typename T, int BASIS>
 cudaError_t step_dispatch_um(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
-                             int um, int nv, double* part) {
+                             int um, int nv, double* part, int64_t* nblk) {
     switch (um) {
-        case UM_ZERO: return step_dispatch_nv<T, UM_ZERO, BASIS>(src, dst, a, st, nv, part);
-        case UM_FLUID: return step_dispatch_nv<T, UM_FLUID, BASIS>(src, dst, a, st, nv, part);
+        case UM_ZERO:
+            return step_dispatch_nv<T, UM_ZERO, BASIS>(src, dst, a, st, nv, part, nblk);
+        case UM_FLUID:
+            return step_dispatch_nv<T, UM_FLUID, BASIS>(src, dst, a, st, nv, part, nblk);
         case UM_ANALYTIC:
-            return step_dispatch_nv<T, UM_ANALYTIC, BASIS>(src, dst, a, st, nv, part);
-        case UM_FIELD: return step_dispatch_nv<T, UM_FIELD, BASIS>(src, dst, a, st, nv, part);
+            return step_dispatch_nv<T, UM_ANALYTIC, BASIS>(src, dst, a, st, nv, part, nblk);
+        case UM_FIELD:
+            return step_dispatch_nv<T, UM_FIELD, BASIS>(src, dst, a, st, nv, part, nblk);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <typename T>
 cudaError_t step_dispatch_basis(const void* src, void* dst, const StepArgs& a, cudaStream_t st,
-                                int um, int nv, int basis, double* part) {
-    return basis == 0 ? step_dispatch_um<T, 0>(src, dst, a, st, um, nv, part)
-                      : step_dispatch_um<T, 1>(src, dst, a, st, um, nv, part);
+                                int um, int nv, int basis, double* part, int64_t* nblk) {
+    return basis == 0 ? step_dispatch_um<T, 0>(src, dst, a, st, um, nv, part, nblk)
+                      : step_dispatch_um<T, 1>(src, dst, a, st, um, nv, part, nblk);
 }
 
 }  // namespace
@@ -482,13 +528,16 @@ int step_vector_width(int storage, int nx) {
 namespace {
 
 cudaError_t step_storage(int storage, int um, int nv, const void* src, void* dst,
-                         const StepArgs& a, cudaStream_t st, int basis, double* part) {
+                         const StepArgs& a, cudaStream_t st, int basis, double* part,
+                         int64_t* nblk = nullptr) {
     switch (storage) {
-        case kStoreF32: return step_dispatch_basis<float>(src, dst, a, st, um, nv, basis, part);
+        case kStoreF32:
+            return step_dispatch_basis<float>(src, dst, a, st, um, nv, basis, part, nblk);
         case kStoreF16:
-            return step_dispatch_basis<__half>(src, dst, a, st, um, nv, basis, part);
+            return step_dispatch_basis<__half>(src, dst, a, st, um, nv, basis, part, nblk);
         case kStoreBF16:
-            return step_dispatch_basis<__nv_bfloat16>(src, dst, a, st, um, nv, basis, part);
+            return step_dispatch_basis<__nv_bfloat16>(src, dst, a, st, um, nv, basis, part,
+                                                      nblk);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -514,10 +563,10 @@ cudaError_t launch_step_conserved(int storage, int um, int nv, const void* src, 
                                   double jx_ref, double jy_ref, double lambda,
                                   double* partials, double* out) {
     if (nv < 2 || !partials || !out) return cudaErrorInvalidValue;
-    cudaError_t e = step_storage(storage, um, nv, src, dst, a, st, basis, partials);
+    int64_t nblk = 0;  // block slots the step writes (at most step_sum_blocks)
+    cudaError_t e = step_storage(storage, um, nv, src, dst, a, st, basis, partials, &nblk);
     if (e != cudaSuccess) return e;
     // the step's block partials, a fixed 256 per block of a middle level, then one block
-    const int64_t nblk = step_sum_blocks(a.nx, a.ny, nv);
     const int64_t mid = (nblk + kReduceThreads - 1) / kReduceThreads;
     double* mids = partials + 4 * nblk;
     k_sum_partials<<<(unsigned)mid, kReduceThreads, 0, st>>>(partials, nblk, mids);
@@ -591,8 +640,17 @@ cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, i
 }
 
 int conserved_blocks(int64_t n) {
-    int64_t b = (n + kReduceThreads - 1) / kReduceThreads;
-    return (int)(b < 1 ? 1 : (b > kReduceMaxBlocks ? kReduceMaxBlocks : b));
+    // no more blocks than are resident at once: a partial second wave of the reduction
+    // blocks ran at a third of the occupancy
+    static std::atomic<int> resident[kMaxDevicesOcc];
+    int full = 0;
+    if (resident_blocks(k_conserved_partial<float>, resident, kReduceThreads, 0, 8, &full) !=
+            cudaSuccess || full < 1 || full > kReduceMaxBlocks) {
+        cudaGetLastError();
+        full = kReduceMaxBlocks;
+    }
+    const int64_t b = (n + kReduceThreads - 1) / kReduceThreads;
+    return (int)(b < 1 ? 1 : (b > full ? full : b));
 }
 
 cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int64_t plane,

@@ -9,6 +9,7 @@
 #include "async_copy.cuh"
 #include "d3q19.cuh"
 #include "launch.h"
+#include "occupancy.cuh"
 #include "pdl.cuh"
 #include "pull.cuh"
 
@@ -101,7 +102,7 @@ __device__ __forceinline__ void add_node_sums3(const float g[19], float r[4], in
     r[1] += m.jx;
     r[2] += m.jy;
     r[3] += m.jz;
-    bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy) && isfinite(m.jz)) ? 0 : 1;
+    bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy) && finite_f(m.jz)) ? 0 : 1;
 }
 
 // Sums of v[0..4] over the block (a multiple of 32 threads, at most 1024) into
@@ -145,66 +146,92 @@ __global__ void __launch_bounds__(kThreads3) k_step3(const T* __restrict__ src,
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n = (int64_t)nx * ny * nz;
     const PackLane p = pack_lane<NV>(nx);
-    double sums[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    for (int z = blockIdx.z; z < nz; z += gridDim.z) {
-        for (int y = blockIdx.y; y < ny; y += gridDim.y) {
-            const Rows3 r(y, z, nx, ny, nz);
-            float g[19][NV];
-            const T* s = src;
-            load_pack<T, NV>(s + r.r00 + p.x0, p.act, g[0]);
-            load_from_left<T, NV>(s + 1 * n + r.r00, p.x0, p.xprev, p.act, p.left_edge, g[1]);
-            load_from_right<T, NV>(s + 2 * n + r.r00, p.x0, p.xnext, p.act, p.right_edge, g[2]);
-            load_pack<T, NV>(s + 3 * n + r.rm0 + p.x0, p.act, g[3]);
-            load_pack<T, NV>(s + 4 * n + r.rp0 + p.x0, p.act, g[4]);
-            load_pack<T, NV>(s + 5 * n + r.r0m + p.x0, p.act, g[5]);
-            load_pack<T, NV>(s + 6 * n + r.r0p + p.x0, p.act, g[6]);
-            load_from_left<T, NV>(s + 7 * n + r.rm0, p.x0, p.xprev, p.act, p.left_edge, g[7]);
-            load_from_right<T, NV>(s + 8 * n + r.rp0, p.x0, p.xnext, p.act, p.right_edge, g[8]);
-            load_from_left<T, NV>(s + 9 * n + r.rp0, p.x0, p.xprev, p.act, p.left_edge, g[9]);
-            load_from_right<T, NV>(s + 10 * n + r.rm0, p.x0, p.xnext, p.act, p.right_edge, g[10]);
-            load_from_left<T, NV>(s + 11 * n + r.r0m, p.x0, p.xprev, p.act, p.left_edge, g[11]);
-            load_from_right<T, NV>(s + 12 * n + r.r0p, p.x0, p.xnext, p.act, p.right_edge, g[12]);
-            load_from_left<T, NV>(s + 13 * n + r.r0p, p.x0, p.xprev, p.act, p.left_edge, g[13]);
-            load_from_right<T, NV>(s + 14 * n + r.r0m, p.x0, p.xnext, p.act, p.right_edge, g[14]);
-            load_pack<T, NV>(s + 15 * n + r.rmm + p.x0, p.act, g[15]);
-            load_pack<T, NV>(s + 16 * n + r.rpp + p.x0, p.act, g[16]);
-            load_pack<T, NV>(s + 17 * n + r.rmp + p.x0, p.act, g[17]);
-            load_pack<T, NV>(s + 18 * n + r.rpm + p.x0, p.act, g[18]);
-            if (p.act) {
+    // SUMS: node moments in FP32 runs of kRun packs (32 nodes), each run added in FP64
+    constexpr int kRun = NV >= 32 ? 1 : 32 / NV;
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};
+    float run_r[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
+    auto row = [&](int y, int z) {
+        const Rows3 r(y, z, nx, ny, nz);
+        float g[19][NV];
+        const T* s = src;
+        load_pack<T, NV>(s + r.r00 + p.x0, p.act, g[0]);
+        load_from_left<T, NV>(s + 1 * n + r.r00, p.x0, p.xprev, p.act, p.left_edge, g[1]);
+        load_from_right<T, NV>(s + 2 * n + r.r00, p.x0, p.xnext, p.act, p.right_edge, g[2]);
+        load_pack<T, NV>(s + 3 * n + r.rm0 + p.x0, p.act, g[3]);
+        load_pack<T, NV>(s + 4 * n + r.rp0 + p.x0, p.act, g[4]);
+        load_pack<T, NV>(s + 5 * n + r.r0m + p.x0, p.act, g[5]);
+        load_pack<T, NV>(s + 6 * n + r.r0p + p.x0, p.act, g[6]);
+        load_from_left<T, NV>(s + 7 * n + r.rm0, p.x0, p.xprev, p.act, p.left_edge, g[7]);
+        load_from_right<T, NV>(s + 8 * n + r.rp0, p.x0, p.xnext, p.act, p.right_edge, g[8]);
+        load_from_left<T, NV>(s + 9 * n + r.rp0, p.x0, p.xprev, p.act, p.left_edge, g[9]);
+        load_from_right<T, NV>(s + 10 * n + r.rm0, p.x0, p.xnext, p.act, p.right_edge, g[10]);
+        load_from_left<T, NV>(s + 11 * n + r.r0m, p.x0, p.xprev, p.act, p.left_edge, g[11]);
+        load_from_right<T, NV>(s + 12 * n + r.r0p, p.x0, p.xnext, p.act, p.right_edge, g[12]);
+        load_from_left<T, NV>(s + 13 * n + r.r0p, p.x0, p.xprev, p.act, p.left_edge, g[13]);
+        load_from_right<T, NV>(s + 14 * n + r.r0m, p.x0, p.xnext, p.act, p.right_edge, g[14]);
+        load_pack<T, NV>(s + 15 * n + r.rmm + p.x0, p.act, g[15]);
+        load_pack<T, NV>(s + 16 * n + r.rpp + p.x0, p.act, g[16]);
+        load_pack<T, NV>(s + 17 * n + r.rmp + p.x0, p.act, g[17]);
+        load_pack<T, NV>(s + 18 * n + r.rpm + p.x0, p.act, g[18]);
+        if (p.act) {
+#pragma unroll
+            for (int k = 0; k < NV; ++k) {
+                float h[19];
+#pragma unroll
+                for (int j = 0; j < 19; ++j) h[j] = g[j][k];
+                float ux = 0.0f, uy = 0.0f, uz = 0.0f;
+                if constexpr (UM != UM_ZERO && UM != UM_FLUID)
+                    relative_velocity3<UM>(h, r.r00 + p.x0 + k, n, a, ux, uy, uz);
+                relax_node3<UM>(h, ux, uy, uz, a.s, a.ref);
+#pragma unroll
+                for (int j = 0; j < 19; ++j) g[j][k] = h[j];
+            }
+#pragma unroll
+            for (int j = 0; j < 19; ++j) store_pack<T, NV>(dst + j * n + r.r00 + p.x0, g[j]);
+            if constexpr (SUMS) {
 #pragma unroll
                 for (int k = 0; k < NV; ++k) {
                     float h[19];
 #pragma unroll
                     for (int j = 0; j < 19; ++j) h[j] = g[j][k];
-                    float ux = 0.0f, uy = 0.0f, uz = 0.0f;
-                    if constexpr (UM != UM_ZERO && UM != UM_FLUID)
-                        relative_velocity3<UM>(h, r.r00 + p.x0 + k, n, a, ux, uy, uz);
-                    relax_node3<UM>(h, ux, uy, uz, a.s, a.ref);
-#pragma unroll
-                    for (int j = 0; j < 19; ++j) g[j][k] = h[j];
-                }
-#pragma unroll
-                for (int j = 0; j < 19; ++j) store_pack<T, NV>(dst + j * n + r.r00 + p.x0, g[j]);
-                if constexpr (SUMS) {
-                    float rs[4] = {0.f, 0.f, 0.f, 0.f};  // NV nodes in FP32, then FP64
-                    int bad = 0;
-#pragma unroll
-                    for (int k = 0; k < NV; ++k) {
-                        float h[19];
-#pragma unroll
-                        for (int j = 0; j < 19; ++j) h[j] = g[j][k];
-                        add_node_sums3<T>(h, rs, bad);
-                    }
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) sums[c] += (double)rs[c];
-                    sums[4] += (double)bad;
+                    add_node_sums3<T>(h, run_r, bad);
                 }
             }
         }
+    };
+    if constexpr (!SUMS) {
+        for (int z = blockIdx.z; z < nz; z += gridDim.z)
+            for (int y = blockIdx.y; y < ny; y += gridDim.y) row(y, z);
+    } else {
+        // the block's rows (y fastest, then z) in chunks of kRun; a chunk's FP32 run is
+        // added in FP64 after it, outside the rows' loop (FP64 issues at 2 operations per
+        // clock per SM on this GPU, and predicated adds inside the loop would hold that pipe)
+        int y = blockIdx.y, z = blockIdx.z;
+        while (z < nz) {
+            for (int t = 0; t < kRun && z < nz; ++t) {
+                row(y, z);
+                y += gridDim.y;
+                if (y >= ny) {
+                    y = blockIdx.y;
+                    z += gridDim.z;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sums[c] += (double)run_r[c];
+                run_r[c] = 0.f;
+            }
+        }
     }
-    if constexpr (SUMS)
-        block_sum5(sums, part + 8 * (((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x +
-                                     blockIdx.x));
+    if constexpr (SUMS) {
+        double v[5];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = sums[c] + (double)run_r[c];
+        v[4] = (double)bad;
+        block_sum5(v, part + 8 * (((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x +
+                                  blockIdx.x));
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -284,7 +311,11 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
                                                                    double* __restrict__ part) {
     constexpr int S = kPipeStages;
     constexpr int NPL = kPipeNpl, P = NPL / 2;  // nodes and node pairs per lane
-    double sums[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // SUMS: the stored result's moments
+    // SUMS: the stored result's moments, in FP32 runs of 4 items (32 nodes), each run added
+    // in FP64
+    double sums[4] = {0.0, 0.0, 0.0, 0.0};
+    float run_r[4] = {0.f, 0.f, 0.f, 0.f};
+    int bad = 0;
     pdl_wait_prior();
     pdl_allow_next();
     extern __shared__ __align__(16) unsigned char pipe_smem[];
@@ -371,7 +402,7 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
             if (k == P / 2) copy_group(ahead, fill, std::integral_constant<int, 1>());
         }
     };
-    while (cur.z < nz) {
+    auto item = [&]() {
         if constexpr (Q > 1) {
             copy_group(ahead, fill, I0());  // committed with the other groups, below
             cp_async_wait_all_but<0>();     // every committed group: the item at `cur`
@@ -440,8 +471,6 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
 #pragma unroll
             for (int j = 0; j < 19; ++j) store_raw16<NPL>(dst + j * n + r00 + x0, w[j]);
             if constexpr (SUMS) {
-                float rs[4] = {0.f, 0.f, 0.f, 0.f};  // NPL nodes in FP32, then FP64
-                int bad = 0;
 #pragma unroll
                 for (int k = 0; k < P; ++k) {
                     float lo[19], hi[19];
@@ -451,12 +480,9 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
                         lo[j] = f.x;
                         hi[j] = f.y;
                     }
-                    add_node_sums3<float>(lo, rs, bad);
-                    add_node_sums3<float>(hi, rs, bad);
+                    add_node_sums3<float>(lo, run_r, bad);
+                    add_node_sums3<float>(hi, run_r, bad);
                 }
-#pragma unroll
-                for (int c = 0; c < 4; ++c) sums[c] += (double)rs[c];
-                sums[4] += (double)bad;
             }
         } else if constexpr (Q > 1) {
 #pragma unroll
@@ -468,8 +494,29 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
         fill = fill == S - 1 ? 0 : fill + 1;
         cur = advance(cur);
         stage = stage == S - 1 ? 0 : stage + 1;
+    };
+    if constexpr (!SUMS) {
+        while (cur.z < nz) item();
+    } else {
+        // items in chunks of 32 / NPL (32 nodes per lane); a chunk's FP32 run is added in
+        // FP64 after it, outside the items' loop (FP64 issues at 2 operations per clock per
+        // SM on this GPU, and predicated adds inside the loop would hold that pipe)
+        while (cur.z < nz) {
+            for (int t = 0; t < 32 / NPL && cur.z < nz; ++t) item();
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sums[c] += (double)run_r[c];
+                run_r[c] = 0.f;
+            }
+        }
     }
-    if constexpr (SUMS) block_sum5(sums, part + 8 * (int64_t)blockIdx.x);
+    if constexpr (SUMS) {
+        double v[5];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) v[c] = sums[c] + (double)run_r[c];
+        v[4] = (double)bad;
+        block_sum5(v, part + 8 * (int64_t)blockIdx.x);
+    }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -663,36 +710,36 @@ __global__ void k_moments3(const T* __restrict__ src, float* __restrict__ rho,
     }
 }
 
-// FP64 sums of (sum g, sum c g (3), non-finite nodes), 8 doubles per block (5 used).
+// FP64 sums of (sum g, sum c g (3), non-finite nodes), 8 doubles per block (5 used). Six
+// blocks per SM, the residency of the D2Q9 reduction that sets the shared block count
+// (conserved_blocks), so that no partial wave runs.
 template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) k_conserved3_partial(const T* __restrict__ src,
+__global__ void __launch_bounds__(kReduceThreads, 6) k_conserved3_partial(const T* __restrict__ src,
                                                                        int64_t n, int64_t plane,
                                                                        double* __restrict__ part) {
+    // FP32 runs of up to 32 nodes, each run added in FP64 after its loop (as in the D2Q9
+    // reduction)
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    float r[4] = {0.f, 0.f, 0.f, 0.f};
-    int run = 0, bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        float g[19];
+    int bad = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    while (i < n) {
+        float r[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int k = 0; k < 32 && i < n; ++k, i += stride) {
+            float g[19];
 #pragma unroll
-        for (int j = 0; j < 19; ++j) g[j] = to_f(src[j * plane + i]);
-        const NodeMoments3 m = node_moments3(g);
-        r[0] += m.drho;
-        r[1] += m.jx;
-        r[2] += m.jy;
-        r[3] += m.jz;
-        bad += (isfinite(m.drho) && isfinite(m.jx) && isfinite(m.jy) && isfinite(m.jz)) ? 0 : 1;
-        if (++run == 32) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                v[c] += (double)r[c];
-                r[c] = 0.f;
-            }
-            run = 0;
+            for (int j = 0; j < 19; ++j) g[j] = to_f(src[j * plane + i]);
+            const NodeMoments3 m = node_moments3(g);
+            r[0] += m.drho;
+            r[1] += m.jx;
+            r[2] += m.jy;
+            r[3] += m.jz;
+            bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy) && finite_f(m.jz)) ? 0
+                                                                                          : 1;
         }
-    }
 #pragma unroll
-    for (int c = 0; c < 4; ++c) v[c] += (double)r[c];
+        for (int c = 0; c < 4; ++c) v[c] += (double)r[c];
+    }
     v[4] = (double)bad;
     __shared__ double sh[kReduceThreads / 32][5];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
@@ -769,6 +816,7 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 // k_step3_pipe_pairs. Both number rows in 32 bits (ny * nz < 2^31, which any 16-bit
 // lattice of 4 or more nodes per row that fits in device memory meets); beyond that
 // 2-node packs run.
+
 // Form of 1/rho in the 16-bit pipelines, measured on GB300 at 256^3 (8-node packs, of copy
 // bandwidth): FP16 with u~ = q/rho takes the fast division (0.938, against 0.934 with the
 // approximation and 0.921 correctly rounded); the other kernels keep the correctly rounded
@@ -777,30 +825,6 @@ cudaError_t launch3(K kernel, const void* src, void* dst, const StepArgs3& a, cu
 template <typename T, int UM>
 constexpr int rcp3() {
     return (std::is_same<T, __half>::value && UM == UM_FLUID) ? RCP_DIV : RCP_RN;
-}
-constexpr int kMaxDevices3 = 64;
-
-// Resident blocks of a persistent kernel on the current device (SMs x blocks per SM, at
-// most max_per_sm), found once per device with the shared-memory attribute set and kept
-// in cache[device] (0 = not yet known).
-template <typename... KArgs>
-cudaError_t resident_blocks(void (*kernel)(KArgs...), std::atomic<int>* cache, int threads,
-                            int smem, int max_per_sm, int* full) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    *full = dev < kMaxDevices3 ? cache[dev].load(std::memory_order_relaxed) : 0;
-    if (*full != 0) return cudaSuccess;
-    int sms = 0, per_sm = 0;
-    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
-    if (e != cudaSuccess) return e;
-    per_sm = per_sm < 1 ? 1 : (per_sm > max_per_sm ? max_per_sm : per_sm);
-    *full = per_sm * sms;
-    if (dev < kMaxDevices3) cache[dev].store(*full, std::memory_order_relaxed);
-    return cudaSuccess;
 }
 
 // Blocks of a persistent pipeline over the lattice's row segments: no more than are
@@ -816,7 +840,7 @@ template <typename T, int UM, bool SUMS = false>
 cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
                          double* part = nullptr, int64_t* slots = nullptr) {
     auto kernel = k_step3_pipe<T, UM, rcp3<T, UM>(), SUMS>;
-    static std::atomic<int> resident[kMaxDevices3];
+    static std::atomic<int> resident[kMaxDevicesOcc];
     int full = 0;
     cudaError_t e = resident_blocks(kernel, resident, kPipeWarps * 32, kPipeSmem,
                                     kPipeBlocksPerSm, &full);
@@ -833,7 +857,7 @@ cudaError_t launch_pipe_pairs(const void* src, void* dst, const StepArgs3& a,
                               cudaStream_t st) {
     using C = PipePairs;
     auto kernel = k_step3_pipe_pairs<T, UM, rcp3<T, UM>()>;
-    static std::atomic<int> resident[kMaxDevices3];
+    static std::atomic<int> resident[kMaxDevicesOcc];
     int full = 0;
     cudaError_t e = resident_blocks(kernel, resident, C::kWarps * 32, C::kSmem,
                                     C::kBlocksPerSm, &full);
@@ -856,9 +880,29 @@ cudaError_t step3_sums(const void* src, void* dst, const StepArgs3& a, cudaStrea
             return launch_pipe3<T, UM, true>(src, dst, a, st, part, slots);
     } else {
         if (nv == 4) {
-            const dim3 g = step3_grid(a, 4, false);
+            // as many blocks as are resident at once, planes (then rows) strided over them,
+            // so that each block's FP64 reduction runs once (one row per block spent longer
+            // in the reductions than in the step)
+            auto kernel = k_step3<T, 4, UM, true>;
+            const dim3 b = step3_block(a.nx, 4, false);
+            static std::atomic<int> resident[kMaxDevicesOcc];
+            int full = 0;
+            cudaError_t e = resident_blocks(kernel, resident, (int)(b.x * b.y), 0, 32, &full);
+            if (e != cudaSuccess) return e;
+            dim3 g = step3_grid(a, 4, false);
+            const int64_t plane_blocks = (int64_t)g.x * g.y;
+            if (plane_blocks >= full) {
+                const int64_t gy = full / g.x;
+                g.y = (unsigned)(gy < 1 ? 1 : (gy < g.y ? gy : g.y));
+                g.z = 1;
+            } else {
+                const int64_t gz = full / plane_blocks;
+                g.z = (unsigned)(gz < g.z ? gz : g.z);
+            }
             *slots = (int64_t)g.x * g.y * g.z;
-            return launch3(k_step3<T, 4, UM, true>, src, dst, a, st, 4, false, part);
+            e = launch_pdl(kernel, g, b, st, static_cast<const T*>(src), static_cast<T*>(dst), a,
+                           part);
+            return e != cudaSuccess ? e : cudaGetLastError();
         }
     }
     return cudaErrorNotSupported;
