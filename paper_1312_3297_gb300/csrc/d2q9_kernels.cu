@@ -338,30 +338,42 @@ __global__ void k_moments(const T* __restrict__ src, float* __restrict__ rho,
 }
 
 // Nodes 0 .. n-1 of a state whose planes are `plane` elements apart (plane = n for a whole
-// lattice; larger for the interior layers of a slab).
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads) k_conserved_partial(const T* __restrict__ src,
-                                                                      int64_t n, int64_t plane,
-                                                                      double* __restrict__ part) {
+// lattice; larger for the interior layers of a slab), NV consecutive nodes per thread and
+// pack (one vector load per plane; n and plane multiples of NV, planes NV-aligned). At
+// least kReduceMinBlocks blocks fit on an SM, the count conserved_blocks launches.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kReduceThreads, kReduceMinBlocks)
+    k_conserved_partial(const T* __restrict__ src, int64_t n, int64_t plane,
+                        double* __restrict__ part) {
     // Node moments are FP32; each thread adds runs of up to 32 of them in FP32 and the
     // runs in FP64 (a run of 32 loses < 1e-6 relative). The FP64 adds sit after the run's
     // loop rather than under a condition inside it: FP64 issues at 2 operations per clock
     // per SM on this GPU, and a predicated add inside the loop held that pipe every node.
+    constexpr int kRunPacks = NV >= 32 ? 1 : 32 / NV;
     double v[4] = {0.0, 0.0, 0.0, 0.0};
     int bad = 0;
+    const int64_t packs = n / NV;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    while (i < n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // pack index
+    while (i < packs) {
         float r[3] = {0.f, 0.f, 0.f};
-        for (int k = 0; k < 32 && i < n; ++k, i += stride) {
-            float g[9];
+        for (int k = 0; k < kRunPacks && i < packs; ++k, i += stride) {
+            float g[9][NV];
 #pragma unroll
-            for (int j = 0; j < 9; ++j) g[j] = to_f(src[j * plane + i]);
-            const NodeMoments m = node_moments(g);
-            r[0] += m.drho;
-            r[1] += m.jx;
-            r[2] += m.jy;
-            bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy)) ? 0 : 1;
+            for (int j = 0; j < 9; ++j)
+                PackCvt<T, NV>::in(*reinterpret_cast<const Pack<T, NV>*>(src + j * plane + i * NV),
+                                   g[j]);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                float h[9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) h[j] = g[j][q];
+                const NodeMoments m = node_moments(h);
+                r[0] += m.drho;
+                r[1] += m.jx;
+                r[2] += m.jy;
+                bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy)) ? 0 : 1;
+            }
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) v[c] += (double)r[c];
@@ -640,15 +652,18 @@ cudaError_t launch_moments(int storage, const void* src, float* rho, float* u, i
 }
 
 int conserved_blocks(int64_t n) {
-    // no more blocks than are resident at once: a partial second wave of the reduction
-    // blocks ran at a third of the occupancy
-    static std::atomic<int> resident[kMaxDevicesOcc];
-    int full = 0;
-    if (resident_blocks(k_conserved_partial<float>, resident, kReduceThreads, 0, 8, &full) !=
-            cudaSuccess || full < 1 || full > kReduceMaxBlocks) {
-        cudaGetLastError();
-        full = kReduceMaxBlocks;
+    // kReduceMinBlocks per SM, which every reduction kernel's launch bounds guarantee: no
+    // partial second wave (one ran at a third of the occupancy)
+    static std::atomic<int> sms_of[kMaxDevicesOcc];
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        sms = dev < kMaxDevicesOcc ? sms_of[dev].load(std::memory_order_relaxed) : 0;
+        if (sms == 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) ==
+                            cudaSuccess && dev < kMaxDevicesOcc)
+            sms_of[dev].store(sms, std::memory_order_relaxed);
     }
+    int64_t full = (int64_t)(sms > 0 ? sms : 152) * kReduceMinBlocks;
+    if (full > kReduceMaxBlocks) full = kReduceMaxBlocks;
     const int64_t b = (n + kReduceThreads - 1) / kReduceThreads;
     return (int)(b < 1 ? 1 : (b > full ? full : b));
 }
@@ -662,21 +677,42 @@ cudaError_t launch_mean_flow(const float* rho, const float* u, int64_t n, int64_
     return cudaGetLastError();
 }
 
+namespace {
+
+// The widest pack (up to 16 bytes) that n, plane and the base address allow.
+template <typename T>
+int reduce_width(const void* src, int64_t n, int64_t plane, int widest) {
+    for (int nv = widest; nv > 1; nv >>= 1)
+        if (n % nv == 0 && plane % nv == 0 &&
+            reinterpret_cast<uintptr_t>(src) % (nv * sizeof(T)) == 0)
+            return nv;
+    return 1;
+}
+
+template <typename T>
+void launch_conserved_t(const void* src, int64_t n, int64_t plane, double* partials, int nblk,
+                        cudaStream_t st) {
+    const T* s = static_cast<const T*>(src);
+    const int nv = reduce_width<T>(src, n, plane, sizeof(T) == 4 ? 4 : 8);
+    auto run = [&](auto kernel) { kernel<<<nblk, kReduceThreads, 0, st>>>(s, n, plane, partials); };
+    if constexpr (sizeof(T) == 2) {
+        if (nv == 8) return run(k_conserved_partial<T, 8>);
+    }
+    if (nv >= 4) return run(k_conserved_partial<T, 4>);
+    if (nv == 2) return run(k_conserved_partial<T, 2>);
+    run(k_conserved_partial<T, 1>);
+}
+
+}  // namespace
+
 cudaError_t launch_conserved(int storage, const void* src, int64_t n, int64_t plane,
                              double rho_ref, double jx_ref, double jy_ref, double lambda,
                              double* partials, int nblk, double* out, cudaStream_t st) {
     switch (storage) {
-        case kStoreF32:
-            k_conserved_partial<float><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const float*>(src), n, plane, partials);
-            break;
-        case kStoreF16:
-            k_conserved_partial<__half><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __half*>(src), n, plane, partials);
-            break;
+        case kStoreF32: launch_conserved_t<float>(src, n, plane, partials, nblk, st); break;
+        case kStoreF16: launch_conserved_t<__half>(src, n, plane, partials, nblk, st); break;
         case kStoreBF16:
-            k_conserved_partial<__nv_bfloat16><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __nv_bfloat16*>(src), n, plane, partials);
+            launch_conserved_t<__nv_bfloat16>(src, n, plane, partials, nblk, st);
             break;
         default: return cudaErrorInvalidValue;
     }

@@ -710,32 +710,43 @@ __global__ void k_moments3(const T* __restrict__ src, float* __restrict__ rho,
     }
 }
 
-// FP64 sums of (sum g, sum c g (3), non-finite nodes), 8 doubles per block (5 used). Six
-// blocks per SM, the residency of the D2Q9 reduction that sets the shared block count
-// (conserved_blocks), so that no partial wave runs.
-template <typename T>
-__global__ void __launch_bounds__(kReduceThreads, 6) k_conserved3_partial(const T* __restrict__ src,
-                                                                       int64_t n, int64_t plane,
-                                                                       double* __restrict__ part) {
+// FP64 sums of (sum g, sum c g (3), non-finite nodes), 8 doubles per block (5 used), NV
+// consecutive nodes per thread and pack (n and plane multiples of NV, planes NV-aligned).
+// At least kReduceMinBlocks blocks fit on an SM, the count conserved_blocks launches.
+template <typename T, int NV>
+__global__ void __launch_bounds__(kReduceThreads, kReduceMinBlocks)
+    k_conserved3_partial(const T* __restrict__ src, int64_t n, int64_t plane,
+                         double* __restrict__ part) {
     // FP32 runs of up to 32 nodes, each run added in FP64 after its loop (as in the D2Q9
     // reduction)
+    constexpr int kRunPacks = NV >= 32 ? 1 : 32 / NV;
     double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     int bad = 0;
+    const int64_t packs = n / NV;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    while (i < n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;  // pack index
+    while (i < packs) {
         float r[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int k = 0; k < 32 && i < n; ++k, i += stride) {
-            float g[19];
+        for (int k = 0; k < kRunPacks && i < packs; ++k, i += stride) {
+            float g[19][NV];
 #pragma unroll
-            for (int j = 0; j < 19; ++j) g[j] = to_f(src[j * plane + i]);
-            const NodeMoments3 m = node_moments3(g);
-            r[0] += m.drho;
-            r[1] += m.jx;
-            r[2] += m.jy;
-            r[3] += m.jz;
-            bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy) && finite_f(m.jz)) ? 0
-                                                                                          : 1;
+            for (int j = 0; j < 19; ++j)
+                PackCvt<T, NV>::in(*reinterpret_cast<const Pack<T, NV>*>(src + j * plane + i * NV),
+                                   g[j]);
+#pragma unroll
+            for (int q = 0; q < NV; ++q) {
+                float h[19];
+#pragma unroll
+                for (int j = 0; j < 19; ++j) h[j] = g[j][q];
+                const NodeMoments3 m = node_moments3(h);
+                r[0] += m.drho;
+                r[1] += m.jx;
+                r[2] += m.jy;
+                r[3] += m.jz;
+                bad += (finite_f(m.drho) && finite_f(m.jx) && finite_f(m.jy) && finite_f(m.jz))
+                           ? 0
+                           : 1;
+            }
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) v[c] += (double)r[c];
@@ -1063,21 +1074,36 @@ cudaError_t launch_moments3(int storage, const void* src, float* rho, float* u, 
     return cudaGetLastError();
 }
 
+namespace {
+
+// Packs of up to 8 bytes per plane, 4 bytes for BF16 (wider packs of 19 planes spill at the
+// reduction's register budget), as wide as n, plane and the base address allow.
+template <typename T>
+void launch_conserved3_t(const void* src, int64_t n, int64_t plane, double* partials,
+                         int nblk, cudaStream_t st) {
+    const T* s = static_cast<const T*>(src);
+    int nv = std::is_same<T, __nv_bfloat16>::value ? 2 : 8 / (int)sizeof(T);
+    while (nv > 1 && !(n % nv == 0 && plane % nv == 0 &&
+                       reinterpret_cast<uintptr_t>(src) % (nv * sizeof(T)) == 0))
+        nv >>= 1;
+    auto run = [&](auto kernel) { kernel<<<nblk, kReduceThreads, 0, st>>>(s, n, plane, partials); };
+    if constexpr (std::is_same<T, __half>::value) {
+        if (nv == 4) return run(k_conserved3_partial<T, 4>);
+    }
+    if (nv >= 2) return run(k_conserved3_partial<T, 2>);
+    run(k_conserved3_partial<T, 1>);
+}
+
+}  // namespace
+
 cudaError_t launch_conserved3(int storage, const void* src, int64_t n, int64_t plane,
                               const StoreRef3& ref, double lambda, double* partials, int nblk,
                               double* out, cudaStream_t st) {
     switch (storage) {
-        case kStoreF32:
-            k_conserved3_partial<float><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const float*>(src), n, plane, partials);
-            break;
-        case kStoreF16:
-            k_conserved3_partial<__half><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __half*>(src), n, plane, partials);
-            break;
+        case kStoreF32: launch_conserved3_t<float>(src, n, plane, partials, nblk, st); break;
+        case kStoreF16: launch_conserved3_t<__half>(src, n, plane, partials, nblk, st); break;
         case kStoreBF16:
-            k_conserved3_partial<__nv_bfloat16><<<nblk, kReduceThreads, 0, st>>>(
-                static_cast<const __nv_bfloat16*>(src), n, plane, partials);
+            launch_conserved3_t<__nv_bfloat16>(src, n, plane, partials, nblk, st);
             break;
         default: return cudaErrorInvalidValue;
     }

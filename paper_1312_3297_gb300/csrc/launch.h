@@ -16,6 +16,8 @@ constexpr int kReduceThreads = 256;
 // it). A compile-time constant because it sizes the fixed scratch of
 // lbmrv_conserved_noalloc.
 constexpr int kReduceMaxBlocks = 152 * 8;
+// Blocks of the reduction kernels resident on one SM, at least (their launch bounds).
+constexpr int kReduceMinBlocks = 4;
 
 // Blocks of a grid-stride kernel over n items with `threads` per block: enough for every
 // item, at most 16 per SM of the current device (found once per device).
