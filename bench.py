@@ -187,9 +187,10 @@ def default_width(lattice: str, storage: str, nx: int) -> int:
     return widest
 
 
-def kernel_label(lattice: str, storage: str, nx: int, mode: str, scheme: str = "rv") -> str:
+def kernel_label(lattice: str, storage: str, nx: int, mode: str, scheme: str = "rv",
+                 width: int = 0) -> str:
     """Name of the step kernel the library launches for this configuration."""
-    nv = default_width(lattice, storage, nx)
+    nv = width or default_width(lattice, storage, nx)
     if lattice == "d2q9":
         name = "k_step_vec" if scheme == "rv" else "k_step_vec, Geier basis"
     elif storage == "fp32":
@@ -287,6 +288,8 @@ def gpu_arm(args):
         d3 = inp.taylor_green_3d(size, size, size, u0=0.04)
         sim = D3Q19(size, size, size, [0, 0, 0, 0, 1.2] + [1.7] * 5 + [1.9] * 6 + [1.4] * 3,
                     mode="fluid" if args.mode == "prescribed" else args.mode, storage=args.storage)
+        if args.width:
+            sim.set_kernel_width(args.width)
         sim.init_equilibrium(torch.as_tensor(d3["rho"], dtype=torch.float32),
                              *(torch.as_tensor(c, dtype=torch.float32) for c in d3["u"]))
         del d3
@@ -313,6 +316,8 @@ def gpu_arm(args):
         else:
             scheme = D2Q9
         sim = make_sim(torch, scheme, inp, args.storage, args.mode, size, fields)
+        if args.width:
+            sim.set_kernel_width(args.width)
     sim.step(args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local) if rank == 0 else None
@@ -359,7 +364,7 @@ def gpu_arm(args):
     achieved = bpn * n / (per_step_ms * 1e-3) / 1e9
     headline = (size == L and args.storage == "fp32" and args.mode == "prescribed"
                 and args.lattice == "d2q9" and args.decomp == "replicas"
-                and args.scheme == "rv")
+                and args.scheme == "rv" and not args.width)
     out = None
     if rank == 0:
         extras = {}
@@ -418,7 +423,7 @@ def gpu_arm(args):
                          "peak_kind": peak_kind,
                          "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                          "kernel": kernel_label(args.lattice, args.storage, size, args.mode,
-                                                args.scheme)},
+                                                args.scheme, args.width)},
             "clocks": clock_info,
             "e2e": e2e,
             # one step kernel per step and rank; a slab adds its pack and unpack kernels
@@ -894,6 +899,9 @@ def main():
     ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
                     help="N > 1: independent replicas (default), or one lattice of N stacked "
                          "Taylor-Green cells split into slabs with a halo exchange per step")
+    ap.add_argument("--width", type=int, default=0,
+                    help="nodes per thread of the step kernel (0: the library's choice; "
+                         "profiling captures)")
     ap.add_argument("--scheme", default="rv", choices=["rv", "cascaded"],
                     help="D2Q9 relaxation of the timed run: the relative-velocity scheme's "
                          "orthogonal basis (rv) or Geier's cascaded basis (profiling captures)")
