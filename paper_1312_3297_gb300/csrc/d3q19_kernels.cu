@@ -304,7 +304,7 @@ constexpr int pipe_plane_groups() {
     return UM == UM_ZERO ? 4 : std::is_same<T, __nv_bfloat16>::value ? 2 : 1;
 }
 
-template <typename T, int UM, int RCP, bool SUMS = false>
+template <typename T, int UM, int RCP, bool SUMS = false, bool TAILS = false>
 __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pipe(const T* __restrict__ src,
                                                                    T* __restrict__ dst,
                                                                    StepArgs3 a,
@@ -322,7 +322,16 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nx = a.nx, ny = a.ny, nz = a.nz;
     const int64_t n = (int64_t)nx * ny * nz;
-    const int segs = (nx + kPipeSeg - 1) / kPipeSeg;
+    // TAILS (nx not a multiple of kPipeSeg): `segs` counts a row's full segments, and the
+    // rows' short last segments (tail_lanes lanes each) are packed rows_per_tail rows to an
+    // item after all full segments, lane l of such an item taking row base + l / tail_lanes
+    // (with one row per item they left most lanes idle). Without TAILS a row has segs
+    // segments.
+    const int segs = TAILS ? nx / kPipeSeg : (nx + kPipeSeg - 1) / kPipeSeg;
+    const int tail_lanes = TAILS ? (nx % kPipeSeg) / NPL : 1;
+    const int rows_per_tail = 32 / tail_lanes;
+    const int64_t nrows = (int64_t)ny * nz, nfull = nrows * segs;
+    const int64_t ntail = TAILS ? (nrows + rows_per_tail - 1) / rows_per_tail : 0;
     unsigned char* wbuf = pipe_smem + warp * S * kPipeStage;
 
     // Warp w takes work items (row segments, x fastest, then y, z) w, w + W, w + 2W, ...
@@ -340,7 +349,8 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
         c.y = (int)(row - (int64_t)c.z * ny);
         return c;
     };
-    const Cursor step = split(nwarps);
+    // (TAILS without full segments: a cursor that starts past the last plane)
+    const Cursor step = (TAILS && segs == 0) ? Cursor{0, 0, 0} : split(nwarps);
     auto advance = [&](Cursor c) {
         c.seg += step.seg;
         int carry = c.seg >= segs;
@@ -351,12 +361,27 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
         c.z += step.z + carry;
         return c;
     };
-    // queue the copies of planes [LO, HI) of the item at `c` into buffer `stage`
-    auto copy = [&](const Cursor& c, int stage, auto lo, auto hi) {
+    // TAILS: this lane's row and first node in tail item it - nfull
+    auto tail_work = [&](int64_t it, int& y, int& z, int& x0, bool& ok) {
+        const int64_t t = it - nfull;
+        const int64_t row = t * rows_per_tail + lane / tail_lanes;
+        ok = t < ntail && lane < rows_per_tail * tail_lanes && row < nrows;
+        const int r = ok ? (int)row : 0;  // rows are numbered in 32 bits (launcher)
+        z = r / ny;
+        y = r - z * ny;
+        x0 = segs * kPipeSeg + (lane % tail_lanes) * NPL;
+    };
+    // queue the copies of planes [LO, HI) of the item at `c` (TAILS: at index it) into
+    // buffer `stage`
+    auto copy = [&](const Cursor& c, int64_t it, int stage, auto lo, auto hi) {
         constexpr int LO = decltype(lo)::value, HI = decltype(hi)::value;
-        const int x0 = c.seg * kPipeSeg + lane * NPL;
-        if (c.z < nz && x0 < nx) {
-            const RowNums3 r(c.y, c.z, ny, nz);
+        int y = c.y, z = c.z, x0 = c.seg * kPipeSeg + lane * NPL;
+        bool ok = c.z < nz && x0 < nx;
+        if constexpr (TAILS) {
+            if (c.z >= nz) tail_work(it, y, z, x0, ok);
+        }
+        if (ok) {
+            const RowNums3 r(y, z, ny, nz);
             unsigned char* sb = wbuf + stage * kPipeStage;
             const int xl = (x0 == 0 ? nx : x0) - 2;       // word (x0-2, x0-1), periodic
             const int xr = x0 + NPL >= nx ? 0 : x0 + NPL;  // word after the pack, periodic
@@ -376,44 +401,57 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
     constexpr int Q = S != 2 ? 1 : pipe_plane_groups<T, UM>() < P ? pipe_plane_groups<T, UM>() : P;
     using I0 = std::integral_constant<int, 0>;
     using I19 = std::integral_constant<int, 19>;
-    auto copy_group = [&](const Cursor& c, int stage, auto q) {
+    auto copy_group = [&](const Cursor& c, int64_t it, int stage, auto q) {
         constexpr int G = decltype(q)::value;
-        copy(c, stage, std::integral_constant<int, (19 * G + Q - 1) / Q>(),
+        copy(c, it, stage, std::integral_constant<int, (19 * G + Q - 1) / Q>(),
              std::integral_constant<int, (19 * (G + 1) + Q - 1) / Q>());
     };
 
-    // S-stage ring: the copies of the next S - 1 items are in flight while one is relaxed
-    Cursor cur = split((int64_t)blockIdx.x * kPipeWarps + warp), ahead = cur;
+    // S-stage ring: the copies of the next S - 1 items are in flight while one is relaxed.
+    // TAILS: icur / iahead are the items' indexes (the cursor's position while it is inside
+    // the full segments).
+    const int64_t first = (int64_t)blockIdx.x * kPipeWarps + warp;
+    Cursor cur = (TAILS && segs == 0) ? Cursor{0, 0, nz} : split(first), ahead = cur;
+    int64_t icur = first, iahead = first;
 #pragma unroll
     for (int s = 0; s < S - 1; ++s) {
-        copy(ahead, s, I0(), I19());
+        copy(ahead, iahead, s, I0(), I19());
         cp_async_commit();  // (empty groups keep the count of groups uniform)
         ahead = advance(ahead);
+        if constexpr (TAILS) iahead += nwarps;
     }
+    auto more = [&]() {
+        if constexpr (TAILS) return icur < nfull + ntail;
+        else return cur.z < nz;
+    };
     int stage = 0, fill = S - 1;
     // the groups of the next item issued before node pair k of the current one (k > 0);
     // group 0 goes before the wait for the current item
     auto issue_groups_before = [&](int k) {
         if constexpr (Q == 4) {
-            if (k == 1) copy_group(ahead, fill, std::integral_constant<int, 1>());
-            if (k == 2) copy_group(ahead, fill, std::integral_constant<int, 2>());
-            if (k == 3) copy_group(ahead, fill, std::integral_constant<int, 3>());
+            if (k == 1) copy_group(ahead, iahead, fill, std::integral_constant<int, 1>());
+            if (k == 2) copy_group(ahead, iahead, fill, std::integral_constant<int, 2>());
+            if (k == 3) copy_group(ahead, iahead, fill, std::integral_constant<int, 3>());
         } else if constexpr (Q == 2) {
-            if (k == P / 2) copy_group(ahead, fill, std::integral_constant<int, 1>());
+            if (k == P / 2) copy_group(ahead, iahead, fill, std::integral_constant<int, 1>());
         }
     };
     auto item = [&]() {
         if constexpr (Q > 1) {
-            copy_group(ahead, fill, I0());  // committed with the other groups, below
-            cp_async_wait_all_but<0>();     // every committed group: the item at `cur`
+            copy_group(ahead, iahead, fill, I0());  // committed with the other groups, below
+            cp_async_wait_all_but<0>();             // every committed group: the item at `cur`
         } else {
-            copy(ahead, fill, I0(), I19());
+            copy(ahead, iahead, fill, I0(), I19());
             cp_async_commit();
             cp_async_wait_all_but<S - 1>();  // the oldest group: the item at `cur`
         }
         __syncwarp();
-        const int y = cur.y, z = cur.z, x0 = cur.seg * kPipeSeg + lane * NPL;
-        if (x0 < nx) {
+        int y = cur.y, z = cur.z, x0 = cur.seg * kPipeSeg + lane * NPL;
+        bool ok = x0 < nx;
+        if constexpr (TAILS) {
+            if (cur.z >= nz) tail_work(icur, y, z, x0, ok);
+        }
+        if (ok) {
             const unsigned char* sb = wbuf + stage * kPipeStage;
             const int64_t r00 = (int64_t)(z * ny + y) * nx;
             // pair k of an x-moving plane straddles words k and k + 1 of (left halo, pack)
@@ -493,16 +531,20 @@ __global__ void __launch_bounds__(kPipeWarps * 32, kPipeBlocksPerSm) k_step3_pip
         ahead = advance(ahead);
         fill = fill == S - 1 ? 0 : fill + 1;
         cur = advance(cur);
+        if constexpr (TAILS) {
+            iahead += nwarps;
+            icur += nwarps;
+        }
         stage = stage == S - 1 ? 0 : stage + 1;
     };
     if constexpr (!SUMS) {
-        while (cur.z < nz) item();
+        while (more()) item();
     } else {
         // items in chunks of 32 / NPL (32 nodes per lane); a chunk's FP32 run is added in
         // FP64 after it, outside the items' loop (FP64 issues at 2 operations per clock per
         // SM on this GPU, and predicated adds inside the loop would hold that pipe)
-        while (cur.z < nz) {
-            for (int t = 0; t < 32 / NPL && cur.z < nz; ++t) item();
+        while (more()) {
+            for (int t = 0; t < 32 / NPL && more(); ++t) item();
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 sums[c] += (double)run_r[c];
@@ -847,20 +889,42 @@ inline int pipeline_blocks(const StepArgs3& a, int seg, int warps, int full) {
     return (int)(need < full ? need : full);
 }
 
-template <typename T, int UM, bool SUMS = false>
-cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
-                         double* part = nullptr, int64_t* slots = nullptr) {
-    auto kernel = k_step3_pipe<T, UM, rcp3<T, UM>(), SUMS>;
+// The 8-node pipeline. Rows whose last segment is short enough for two or more to share an
+// item (16 lanes or fewer) run the instance that packs them (TAILS). Measured at
+// 264^3 (tails of 1 lane), FP16 u~ = q/rho / BF16 u~ = q/rho / FP16 u~ = 0: 0.66 / 0.71 /
+// 0.71 of copy bandwidth against 0.52 / 0.52 / 0.60 with one row per item; at 384^3 (16
+// lanes) 0.82 / 0.85 / 0.90 against 0.76 / 0.76 / 0.83. At 200^3 (25 lanes, one row per
+// item either way) the packing instance was slower (0.56-0.59 against 0.71-0.80).
+template <typename T, int UM, bool SUMS, bool TAILS>
+cudaError_t launch_pipe3_t(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                           double* part, int64_t* slots) {
+    auto kernel = k_step3_pipe<T, UM, rcp3<T, UM>(), SUMS, TAILS>;
     static std::atomic<int> resident[kMaxDevicesOcc];
     int full = 0;
     cudaError_t e = resident_blocks(kernel, resident, kPipeWarps * 32, kPipeSmem,
                                     kPipeBlocksPerSm, &full);
     if (e != cudaSuccess) return e;
-    const int blocks = pipeline_blocks(a, kPipeSeg, kPipeWarps, full);
+    const int64_t rows = (int64_t)a.ny * a.nz;  // the kernel's item count:
+    int64_t items = rows * ((a.nx + kPipeSeg - 1) / kPipeSeg);
+    if constexpr (TAILS) {
+        const int rows_per_tail = 32 / ((a.nx % kPipeSeg) / kPipeNpl);
+        items = rows * (a.nx / kPipeSeg) + (rows + rows_per_tail - 1) / rows_per_tail;
+    }
+    const int64_t need = (items + kPipeWarps - 1) / kPipeWarps;
+    const int blocks = (int)(need < full ? need : full);
     if (slots) *slots = blocks;
     e = launch_pdl_smem(kernel, dim3(blocks), dim3(kPipeWarps * 32), kPipeSmem, st,
                         static_cast<const T*>(src), static_cast<T*>(dst), a, part);
     return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename T, int UM, bool SUMS = false>
+cudaError_t launch_pipe3(const void* src, void* dst, const StepArgs3& a, cudaStream_t st,
+                         double* part = nullptr, int64_t* slots = nullptr) {
+    const int tail_lanes = (a.nx % kPipeSeg) / kPipeNpl;
+    return tail_lanes == 0 || tail_lanes > 16
+               ? launch_pipe3_t<T, UM, SUMS, false>(src, dst, a, st, part, slots)
+               : launch_pipe3_t<T, UM, SUMS, true>(src, dst, a, st, part, slots);
 }
 
 template <typename T, int UM>

@@ -89,11 +89,14 @@ def test_16bit_3d_every_width(storage, u_tol, mode):
 
 
 @pytest.mark.parametrize("storage,u_tol", [("fp16", None), ("bf16", BF16_SINE_U_TOL)])
-@pytest.mark.parametrize("shape", [(264, 3, 2), (552, 2, 3)])
+@pytest.mark.parametrize("shape", [(264, 3, 2), (552, 2, 3), (392, 2, 3), (200, 3, 2)])
 def test_16bit_3d_rows_of_several_segments(storage, u_tol, shape):
     """Rows longer than one 256-node segment of the staged 8-node-pack kernel, the last
-    segment short (one pack; five packs), with every x-moving population crossing the
-    segment boundaries: the kernel against the oracle and bit for bit against 4-node packs."""
+    segment short, with every x-moving population crossing the segment boundaries: the
+    kernel against the oracle and bit for bit against 4-node packs. Short last segments of
+    one and five packs are packed several rows to an item (the rows of an item in different
+    y and z); those of 17 packs (392) and a single segment of 25 (200) keep one row per
+    item."""
     outs = {w: _check(shape, "fluid", 12, tol=2e-3, u_tol=u_tol, seed=5, storage=storage,
                       width=w)
             for w in (4, 8)}
