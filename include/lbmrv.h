@@ -223,8 +223,9 @@ LBMRV_API int lbmrv_moments_host(lbmrv_t h, float* rho_host, float* u_host);
 
 /* Global sums of the current state, accumulated in FP64: out_host[0] = sum rho,
  * out_host[1..2] = sum q_x, sum q_y (physical units), out_host[3] = number of nodes holding
- * a non-finite value. Synchronous. Returns LBMRV_E_NONFINITE (after filling out_host)
- * when out_host[3] > 0. */
+ * a non-finite value. Node moments are FP32; each thread adds runs of up to 32 of them in
+ * FP32 and the runs in FP64, in a fixed order (deterministic). Synchronous. Returns
+ * LBMRV_E_NONFINITE (after filling out_host) when out_host[3] > 0. */
 LBMRV_API int lbmrv_conserved(lbmrv_t h, double out_host[4]);
 
 /* Same for any lattice with all momentum components: out_host = {sum rho, sum q_x,
@@ -237,10 +238,11 @@ LBMRV_API int lbmrv_conserved3(lbmrv_t h, double out_host[5]);
  * lattice). Fused for D2Q9 at vector kernel widths (nodes per thread >= 2) and for D3Q19
  * at its default widths (FP32: 4 nodes per thread; FP16/BF16: 8); other widths run the
  * step, then lbmrv_conserved3's own pass. The sums are added in a fixed
- * order (deterministic for a given width); they agree with lbmrv_conserved3 of the same
- * state to FP64 rounding of FP32 node moments. The first call, and a call after the
- * lattice or width changed, allocates 32-64 bytes per step-kernel block of scratch,
- * kept until lbmrv_destroy. Synchronous. Returns LBMRV_E_NONFINITE (after filling
+ * order (deterministic for a given width and GPU), in FP32 runs of 32 node moments added in
+ * FP64; they agree with lbmrv_conserved3 of the same state to the rounding of those runs
+ * (about 1e-7 relative to a run's magnitude). The first call, and a call after the lattice
+ * or width changed, allocates 32-64 bytes per step-kernel block of scratch, kept until
+ * lbmrv_destroy. Synchronous. Returns LBMRV_E_NONFINITE (after filling
  * out_host) when non-finite nodes were found, LBMRV_E_INVAL for n < 1. */
 LBMRV_API int lbmrv_step_conserved(lbmrv_t h, int64_t n, double out_host[5]);
 
