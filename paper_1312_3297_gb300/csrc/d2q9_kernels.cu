@@ -138,13 +138,28 @@ __global__ void __launch_bounds__(256) k_step_scalar(const T* __restrict__ src,
 // bandwidth instead of 0.98 (measured at 8192^2; the stored field runs faster with four).
 // A minimum of 0 blocks leaves every other instance's register budget as without one (same
 // allocation); a minimum of 1 lets the orthogonal-basis 8-node packs grow to 194 registers.
-// The instances with fused sums (not the timed step) keep the compiler's choice.
-template <int BASIS, int NV, int UM, bool SUMS>
+// With 16-bit 4-node packs Geier's basis also relaxes node pairs, at eight blocks per SM,
+// except with a stored reference field (FP16 / BF16 at 4100^2, of copy bandwidth, paired
+// against node by node: u~ = 0 0.95 / 0.95 against 0.86 / 0.81, u~ = q/rho 0.87 / 0.88
+// against 0.81 / 0.77, the analytic field 0.83 / 0.83 against 0.74 / 0.73, a stored field
+// 0.59 / 0.59 against 0.64 / 0.64). The orthogonal basis is faster node by node there
+// (0.86 against 0.70 with u~ = q/rho).
+// The instances with fused sums (not the timed step) keep the compiler's choice, and with
+// 4-node packs relax node by node.
+template <typename T, int BASIS, int NV, int UM, bool SUMS>
+constexpr bool step_vec_pairs4 =
+    !SUMS && BASIS == 1 && NV == 4 && sizeof(T) == 2 && UM != UM_FIELD;
+template <typename T, int BASIS, int NV, int UM, bool SUMS>
+constexpr bool step_vec_pairs = NV >= 8 || step_vec_pairs4<T, BASIS, NV, UM, SUMS>;
+template <typename T, int BASIS, int NV, int UM, bool SUMS>
 constexpr int step_vec_min_blocks =
-    (BASIS == 1 && NV >= 8 && !SUMS) ? (UM == UM_FIELD ? 4 : 5) : 0;
+    SUMS ? 0
+    : (BASIS == 1 && NV >= 8) ? (UM == UM_FIELD ? 4 : 5)
+    : step_vec_pairs4<T, BASIS, NV, UM, SUMS> ? 8
+                                              : 0;
 
 template <typename T, int NV, int UM, int BASIS, bool SUMS = false>
-__global__ void __launch_bounds__(128, (step_vec_min_blocks<BASIS, NV, UM, SUMS>))
+__global__ void __launch_bounds__(128, (step_vec_min_blocks<T, BASIS, NV, UM, SUMS>))
     k_step_vec(const T* __restrict__ src, T* __restrict__ dst, StepArgs a,
                double* __restrict__ part) {
     pdl_wait_prior();
@@ -172,7 +187,7 @@ __global__ void __launch_bounds__(128, (step_vec_min_blocks<BASIS, NV, UM, SUMS>
                 ux_row = a.amp_t * cospif(a.two_over_ny * (float)(y + a.y_off));
                 load_pack<float, NV>(a.sin_x + p.x0, true, sx);
             }
-            if constexpr (NV >= 8) {
+            if constexpr (step_vec_pairs<T, BASIS, NV, UM, SUMS>) {
                 // Two nodes per packed FP32 instruction. With 8-node packs (16-bit storage)
                 // the step is issue-bound and pairing removes about a third of its
                 // instructions; with 4 or fewer nodes per thread the broadcast constants'
