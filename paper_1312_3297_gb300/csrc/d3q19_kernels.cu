@@ -297,8 +297,8 @@ __device__ __forceinline__ int plane_rownum(const RowNums3& r, int j) {
 // The next item's copies go out in this many plane groups, interleaved with the relaxation
 // of the current item's node pairs (group 0 before it, the others before pairs 1-3 or 2),
 // so that the warps' loads and stores do not reach memory in bursts. Measured on GB300 at
-// 256^3 (MLUPS for 1, 2 and 4 groups): u~ = 0 FP16 74.6 / 82.8 / 86.0 k, BF16 74.5 / 79.6 /
-// 83.4 k; u~ = q/rho FP16 81.3 / 78.6 / 76.4 k, BF16 81.0 / 84.1 / 81.3 k.
+// 256^3 (fraction of copy bandwidth for 1, 2 and 4 groups): u~ = 0 FP16 0.84 / 0.91 / 0.97,
+// BF16 0.84 / 0.90 / 0.94; u~ = q/rho FP16 0.94 / 0.71 / 0.73, BF16 0.92 / 0.95 / 0.92.
 template <typename T, int UM>
 constexpr int pipe_plane_groups() {
     return UM == UM_ZERO ? 4 : std::is_same<T, __nv_bfloat16>::value ? 2 : 1;
