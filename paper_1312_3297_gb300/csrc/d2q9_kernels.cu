@@ -30,7 +30,7 @@ __device__ __forceinline__ void relax_basis(float g[9], float ux, float uy, cons
         relax_node_geier(g, ux, uy, s, ref);
 }
 
-// Two nodes per call (R = F2) for the 8-node packs of 16-bit storage.
+// Two nodes per call (R = F2) for the paired packs of 16-bit storage (step_vec_pairs).
 template <int BASIS, int UM, int RCP>
 __device__ __forceinline__ void relax_basis2(F2 g[9], F2 ux, F2 uy, const Rates& s,
                                              const StoreRef& ref) {
@@ -47,8 +47,8 @@ constexpr bool needs_utilde() {
 
 // Form of 1/rho per kernel variant, measured fastest on GB300 (see recip): the
 // approximation for FP32 storage, the correctly rounded one for 16-bit storage with one
-// node per relaxation call; for the paired 8-node packs the fast division, except without
-// a shift (u~ = 0).
+// node per relaxation call; for paired packs the fast division, except without a shift
+// (u~ = 0).
 template <typename T>
 constexpr int scalar_rcp() {
     return sizeof(T) == 4 ? RCP_APPROX : RCP_RN;
@@ -190,8 +190,8 @@ __global__ void __launch_bounds__(128, (step_vec_min_blocks<T, BASIS, NV, UM, SU
             if constexpr (step_vec_pairs<T, BASIS, NV, UM, SUMS>) {
                 // Two nodes per packed FP32 instruction. With 8-node packs (16-bit storage)
                 // the step is issue-bound and pairing removes about a third of its
-                // instructions; with 4 or fewer nodes per thread the broadcast constants'
-                // extra registers cost more occupancy than the pairing saves (measured).
+                // instructions. With 4 or fewer nodes per thread the broadcast constants'
+                // registers cost more than pairing saves, but for Geier's 16-bit 4-node packs.
 #pragma unroll
                 for (int k = 0; k < NV; k += 2) {
                     F2 h[9];
